@@ -1,0 +1,212 @@
+"""CPU oracle for the NLINV hot path (Schaetz & Uecker, Sec. 3.1, Eq. 2 and Eq. 3, Table 1).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain, complex128 statement of what the GPU library computes.
+Only the test suite, the package smoke check and the benchmark's CPU-baseline leg may import it; the library never
+does, and it shares no code with the CUDA path.
+
+Every step follows the paper's order and notation, with numpy's FFT (pocketfft, double precision) as the one
+library primitive.  Where the paper leaves a detail open, the reading taken here is stated at the function:
+
+* grid arrays are in natural FFT order (origin at index 0), row-major, one ``n`` x ``n`` plane per coil;
+* the unknown is ``x = (rho, chat_1 .. chat_J)``, an array of shape ``(1 + J, n, n)``;
+* the 2D Fourier transform is unitary (``FFT^-1 = FFT^H``);
+* the Sobolev weight of ``W`` is ``w(k) = (1 + a |k|^2)^(-l/2)`` with ``|k|`` in cycles per grid width,
+  ``k_i = g(i)/n`` in ``[-1/2, 1/2)``;
+* Omega is the centred square ``-fov <= g < fov`` (the un-oversampled image of a 2x grid, Sec. 3.2);
+* CG runs a fixed number of iterations from ``dx = 0`` and stops early only when the residual is exactly zero;
+* ``alpha_n = max(alpha_0 q^n, alpha_min)``; a single frame regularises toward its start value.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Setup:
+    """Static problem description: grid side, coil count, field of view and Sobolev parameters."""
+    n: int
+    ncoils: int
+    fov: int
+    a: float = 220.0
+    l: float = 32.0
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Building blocks of Eq. 2
+# ---------------------------------------------------------------------------------------------------------------
+
+def signed_index(n: int) -> np.ndarray:
+    """g(i) = ((i + n/2) mod n) - n/2: the signed coordinate held by natural-order index i."""
+    i = np.arange(n)
+    return (i + n // 2) % n - n // 2
+
+
+def sobolev_weight(n: int, a: float, l: float) -> np.ndarray:
+    """Weight of the weighted Fourier transform W (Sec. 3.1): w(k) = (1 + a |k|^2)^(-l/2), k = g/n per axis."""
+    k = signed_index(n) / n
+    k2 = k[:, None] ** 2 + k[None, :] ** 2
+    return (1.0 + a * k2) ** (-l / 2.0)
+
+
+def omega_mask(n: int, fov: int) -> np.ndarray:
+    """M_Omega of Eq. 2 as a 0/1 array: the centred square -fov <= g < fov in both axes."""
+    g = signed_index(n)
+    inside = ((g >= -fov) & (g < fov)).astype(np.float64)
+    return inside[:, None] * inside[None, :]
+
+
+def fft2u(a: np.ndarray) -> np.ndarray:
+    """Unitary 2D DFT over the last two axes: X[k] = (1/n) sum_x a[x] exp(-2 pi i k.x / n)."""
+    return np.fft.fft2(a, axes=(-2, -1), norm="ortho")
+
+
+def ifft2u(a: np.ndarray) -> np.ndarray:
+    """Inverse (= adjoint) of fft2u."""
+    return np.fft.ifft2(a, axes=(-2, -1), norm="ortho")
+
+
+def inner(u: np.ndarray, v: np.ndarray) -> complex:
+    """Scalar product <u, v> = sum conj(u) v over every entry (Table 1's "A.B")."""
+    return complex(np.vdot(u.ravel(), v.ravel()))
+
+
+def Wi(s: Setup, chat: np.ndarray) -> np.ndarray:
+    """W^-1 of Eq. 2 applied to k-space coil coefficients: c = FFT^-1(w . chat)."""
+    return ifft2u(sobolev_weight(s.n, s.a, s.l) * chat)
+
+
+def WiH(s: Setup, u: np.ndarray) -> np.ndarray:
+    """Adjoint of W^-1: w . FFT(u)."""
+    return sobolev_weight(s.n, s.a, s.l) * fft2u(u)
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# The operator F of Eq. 2, its derivative and adjoint (the three rows F, DF, DF^H of Table 1)
+# ---------------------------------------------------------------------------------------------------------------
+
+def coils(s: Setup, x: np.ndarray) -> np.ndarray:
+    """Image-domain coil sensitivities c_j = W^-1 chat_j of the current estimate."""
+    return Wi(s, x[1:])
+
+
+def channel_sum(c: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """Channel summation of Table 1: sum_j conj(c_j) z_j."""
+    return np.sum(np.conj(c) * z, axis=0)
+
+
+def forward(s: Setup, mask: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """F(x)_j = P FFT(M rho c_j) with c_j = W^-1 chat_j (Eq. 2, applied right to left)."""
+    M = omega_mask(s.n, s.fov)
+    c = coils(s, x)
+    return mask * fft2u(M * x[0] * c)
+
+
+def derivative(s: Setup, mask: np.ndarray, x: np.ndarray, dx: np.ndarray, c: np.ndarray | None = None) -> np.ndarray:
+    """DF_x dx: the Frechet derivative of F at x.  F is bilinear in (rho, chat), so
+    DF_x(drho, dchat)_j = P FFT(M (drho c_j + rho W^-1 dchat_j)).  ``c`` = W^-1 chat of x, if already known."""
+    M = omega_mask(s.n, s.fov)
+    c = coils(s, x) if c is None else c
+    dc = Wi(s, dx[1:])
+    return mask * fft2u(M * (dx[0] * c + x[0] * dc))
+
+
+def adjoint(s: Setup, mask: np.ndarray, x: np.ndarray, r: np.ndarray, c: np.ndarray | None = None) -> np.ndarray:
+    """DF_x^H r: z_j = M FFT^-1(P r_j); image part sum_j conj(c_j) z_j (the channel summation of Table 1);
+    coil part W^-H(conj(rho) z_j).  ``c`` = W^-1 chat of x, if already known."""
+    M = omega_mask(s.n, s.fov)
+    c = coils(s, x) if c is None else c
+    z = M * ifft2u(mask * r)
+    out = np.empty((1 + s.ncoils, s.n, s.n), dtype=np.complex128)
+    out[0] = channel_sum(c, z)
+    out[1:] = WiH(s, np.conj(x[0]) * z)
+    return out
+
+
+def normal(s: Setup, mask: np.ndarray, x: np.ndarray, d: np.ndarray, alpha: float,
+           c: np.ndarray | None = None) -> np.ndarray:
+    """Left-hand operator of Eq. 3: (DF^H DF + alpha I) d."""
+    c = coils(s, x) if c is None else c
+    return adjoint(s, mask, x, derivative(s, mask, x, d, c), c) + alpha * d
+
+
+def simulate(s: Setup, mask: np.ndarray, rho: np.ndarray, coil_img: np.ndarray) -> np.ndarray:
+    """Noiseless gridded data of the signal equation (Eq. 1) for image-domain coils: P FFT(M rho c_j)."""
+    M = omega_mask(s.n, s.fov)
+    return mask * fft2u(M * rho * coil_img)
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Conjugate gradients and the iteratively regularised Gauss-Newton method (Eq. 3)
+# ---------------------------------------------------------------------------------------------------------------
+
+def cg(apply_A, b: np.ndarray, iters: int) -> np.ndarray:
+    """Conjugate gradients for A dx = b, A Hermitian positive definite, from dx = 0, for a fixed count.
+
+    Per iteration (Table 1, row CG: two scalar products): q = A p; alpha = |r|^2 / Re<p, q>; dx += alpha p;
+    r -= alpha q; beta = |r_new|^2 / |r|^2; p = r + beta p.  Stops early only if |r|^2 is exactly zero.
+    """
+    dx = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = inner(r, r).real
+    for _ in range(iters):
+        if rr == 0.0:
+            break
+        q = apply_A(p)
+        pq = inner(p, q).real
+        a = rr / pq
+        dx = dx + a * p
+        r = r - a * q
+        rr_new = inner(r, r).real
+        beta = rr_new / rr
+        p = r + beta * p
+        rr = rr_new
+    return dx
+
+
+def residual(s: Setup, mask: np.ndarray, y: np.ndarray, x: np.ndarray):
+    """r = y - F(x) and its norm (Table 1, row F: one scalar product)."""
+    r = y - forward(s, mask, x)
+    return r, float(np.sqrt(inner(r, r).real))
+
+
+def alpha_schedule(newton_steps: int, alpha0: float, q: float, alpha_min: float = 0.0) -> list:
+    """alpha_n = max(alpha_0 q^n, alpha_min) for n = 0 .. newton_steps-1."""
+    return [max(alpha0 * q ** k, alpha_min) for k in range(newton_steps)]
+
+
+def irgnm(s: Setup, mask: np.ndarray, y: np.ndarray, x0: np.ndarray, xref: np.ndarray | None,
+          newton_steps: int, cg_iters: int, alpha0: float = 1.0, q: float = 0.5, alpha_min: float = 0.0):
+    """Iteratively regularised Gauss-Newton method (Eq. 3).
+
+    For n = 0 .. newton_steps-1: b = DF^H(y - F x_n) - alpha_n (x_n - x_ref); solve
+    (DF^H DF + alpha_n I) dx = b by ``cg_iters`` CG iterations; x_{n+1} = x_n + dx.
+    ``xref=None`` regularises toward x0.  Returns x_N and the residual norms |y - F x_n| for n = 0 .. N.
+    """
+    x = np.array(x0, dtype=np.complex128, copy=True)
+    xr = x.copy() if xref is None else np.asarray(xref, dtype=np.complex128)
+    norms = []
+    for alpha in alpha_schedule(newton_steps, alpha0, q, alpha_min):
+        r0, nr = residual(s, mask, y, x)
+        norms.append(nr)
+        c = coils(s, x)
+        b = adjoint(s, mask, x, r0, c) - alpha * (x - xr)
+        xn = x
+        dx = cg(lambda d: normal(s, mask, xn, d, alpha, c), b, cg_iters)
+        x = x + dx
+    norms.append(residual(s, mask, y, x)[1])
+    return x, norms
+
+
+def realtime_series(s: Setup, masks, ys, x0: np.ndarray, newton_steps: int, cg_iters: int,
+                    alpha0: float = 1.0, q: float = 0.5, alpha_min: float = 0.0):
+    """Frame-sequential reconstruction with temporal regularisation (Sec. 3.2): frame k starts from, and is
+    regularised toward, the result of frame k-1; frame 0 uses x0 for both."""
+    out = []
+    prev = np.array(x0, dtype=np.complex128, copy=True)
+    for mask, y in zip(masks, ys):
+        prev, _ = irgnm(s, mask, y, prev, prev, newton_steps, cg_iters, alpha0, q, alpha_min)
+        out.append(prev)
+    return out
