@@ -1,0 +1,150 @@
+/*
+ * nlinv.h -- C interface of the GB300 NLINV library.
+ *
+ * NLINV (Schaetz & Uecker, "A multi-GPU programming library for real-time applications", Sec. 3.1) reconstructs
+ * an MRI image rho and the coil sensitivities c_j jointly from undersampled multi-coil k-space data y by solving
+ * the nonlinear equation F x = y, with
+ *
+ *     F = P_k FFT M_Omega C W^-1                                                        (Eq. 2)
+ *
+ * by the iteratively regularised Gauss-Newton method
+ *
+ *     (DF^H DF + alpha_n I)(x_{n+1} - x_n) = DF^H (y - F x_n) - alpha_n (x_n - x_ref)  (Eq. 3)
+ *
+ * whose linear systems are solved by conjugate gradients.  Every step runs in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Complex values are interleaved single precision (nlinv_c32).  A "plane" is n x n values, row-major, in
+ *     natural FFT order: index i holds the signed coordinate g(i) = i for i < n/2 and i - n otherwise.
+ *   - The unknown x = (rho, chat_1 .. chat_J) is 1 + J planes: plane 0 is the image rho, planes 1..J the
+ *     k-space coil coefficients chat_j, whose image-domain coil maps are c_j = W^-1 chat_j
+ *     = FFT^-1(w . chat_j) with the Sobolev weight w(k) = (1 + a |k|^2)^(-l/2), |k| in cycles per grid width.
+ *   - k-space data y, residuals and operator outputs in data space are J planes.
+ *   - The sampling pattern P (P_k of Eq. 2) is one n x n plane of bytes, 0 or 1, shared by all coils.
+ *   - M_Omega keeps the centred square -fov <= g < fov of the image (fov = n/4: the un-oversampled image of a 2x
+ *     grid, Sec. 3.2).  FFT is the unitary 2D DFT (FFT^-1 = FFT^H).
+ *   - Work is queued on the context's CUDA stream and returns before it finishes unless stated otherwise.
+ *   - Unless stated otherwise, pointers are DEVICE pointers owned by the caller, valid until the work is done.
+ *   - No entry point throws; every one returns an nlinv_status.  Arguments are checked on the host before any
+ *     work is queued; on error nothing is queued and nlinv_last_error() describes the problem.
+ */
+#ifndef NLINV_H
+#define NLINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NLINV_API __attribute__((visibility("default")))
+#else
+#define NLINV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  float x, y; /* real, imaginary */
+} nlinv_c32;
+
+typedef enum {
+  NLINV_OK = 0,
+  NLINV_EINVAL = 1,      /* bad argument (null pointer, unsupported size, host pointer where a device one is due) */
+  NLINV_ENOMEM = 2,      /* device memory for the context's workspace could not be allocated */
+  NLINV_ECUDA = 3,       /* a CUDA runtime call failed; nlinv_last_error() has its message */
+  NLINV_EBREAKDOWN = 4,  /* CG met Re<p, A p> <= 0 or a non-finite value; the step was skipped (alpha = 0) */
+  NLINV_ETIMEOUT = 5     /* nlinv_wait() gave up before the context's queued work finished */
+} nlinv_status;
+
+/* Problem and solver description (Sec. 3.1-3.2).  Fill with nlinv_default_params() and adjust. */
+typedef struct {
+  int n;             /* grid side (twice the image matrix, Sec. 3.2); see nlinv_supported_size() */
+  int ncoils;        /* J >= 1 (virtual) coils */
+  int newton_steps;  /* Gauss-Newton steps per reconstruction, 1..64 */
+  int cg_iters;      /* CG iterations per Newton step (a fixed count, no tolerance exit), >= 0 */
+  double alpha0;     /* alpha_0 of Eq. 3 (> 0) */
+  double alpha_q;    /* alpha_{n+1} = max(alpha_q alpha_n, alpha_min), 0 < alpha_q <= 1 */
+  double alpha_min;  /* floor of alpha_n, >= 0 */
+  double sobolev_a;  /* a of the Sobolev weight, >= 0 (220 in the real-time setting) */
+  double sobolev_l;  /* l of the Sobolev weight, >= 0 (32) */
+  int fov;           /* half-width of Omega in pixels, 1..n/2 (n/4 by default) */
+  int use_graph;     /* 1: replay each reconstruction as one captured CUDA graph; 0: launch kernel by kernel */
+} nlinv_params;
+
+typedef struct nlinv_ctx nlinv_ctx;
+
+/* 1 if the grid side n has a compiled transform, else 0.  Supported: 16, 32, 48, 64, 80, 96, 128, 160, 192, 256,
+ * 320, 384, 512. */
+NLINV_API int nlinv_supported_size(int n);
+
+/* Defaults for an n x n grid with ncoils coils: 7 Newton steps, 30 CG iterations, alpha_0 = 1, alpha_q = 1/2,
+ * alpha_min = 0, a = 220, l = 32, fov = n/4, use_graph = 1.  EINVAL if p is NULL. */
+NLINV_API nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils);
+
+/* Creates a context on the current CUDA device: validates *params, allocates the device workspace (about
+ * 9 (1+J) n^2 complex values) and builds the transform tables.  stream is a cudaStream_t on which the context
+ * queues its work; NULL makes the context create (and later destroy) a non-blocking stream of its own, since the
+ * legacy default stream cannot be captured into a graph.  On success *out owns the context.  Blocks until set-up
+ * is done.  Errors: EINVAL (bad params, NULL out), ENOMEM, ECUDA. */
+NLINV_API nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** out);
+
+/* Waits for the context's stream, then frees the context and its workspace.  NULL is accepted. */
+NLINV_API nlinv_status nlinv_destroy(nlinv_ctx* ctx);
+
+/* F x of Eq. 2: y_out_j = P FFT(M rho c_j), c_j = W^-1 chat_j.  x: 1+J planes; y_out: J planes. */
+NLINV_API nlinv_status nlinv_forward(nlinv_ctx* ctx, const nlinv_c32* x, const uint8_t* mask, nlinv_c32* y_out);
+
+/* DF_x dx (the derivative of Eq. 3): out_j = P FFT(M (drho c_j + rho W^-1 dchat_j)).  x, dx: 1+J planes;
+ * out: J planes. */
+NLINV_API nlinv_status nlinv_derivative(nlinv_ctx* ctx, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* dx,
+                              nlinv_c32* out);
+
+/* DF_x^H r (the adjoint of Eq. 3): with z_j = M FFT^-1(P r_j), out plane 0 = sum_j conj(c_j) z_j (the channel
+ * summation of Table 1) and out plane j = w . FFT(conj(rho) z_j).  x: 1+J planes; r: J planes; out: 1+J planes. */
+NLINV_API nlinv_status nlinv_adjoint(nlinv_ctx* ctx, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* r,
+                           nlinv_c32* out);
+
+/* The left-hand operator of Eq. 3: out = (DF_x^H DF_x + alpha I) d.  x, d, out: 1+J planes. */
+NLINV_API nlinv_status nlinv_normal(nlinv_ctx* ctx, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* d,
+                          double alpha, nlinv_c32* out);
+
+/* Gridded data of the signal equation (Eq. 1) for image-domain coil maps: y_out_j = P FFT(M rho coil_img_j).
+ * rho: one plane; coil_img: J planes; y_out: J planes.  Used to synthesise test and benchmark data. */
+NLINV_API nlinv_status nlinv_simulate(nlinv_ctx* ctx, const nlinv_c32* rho, const nlinv_c32* coil_img, const uint8_t* mask,
+                            nlinv_c32* y_out);
+
+/* One reconstruction by Eq. 3: params.newton_steps Gauss-Newton steps with alpha_n = max(alpha_0 q^n, alpha_min),
+ * each solved from dx = 0 by params.cg_iters CG iterations; x_{n+1} = x_n + dx.
+ *   y        J planes of gridded data
+ *   mask     sampling pattern
+ *   x_ref    regularisation centre x_ref of Eq. 3 (1+J planes), or NULL to use the start value
+ *   x_inout  on entry the start value x_0, on return x_N (1+J planes)
+ *   resid    NULL, or a HOST array of newton_steps+1 doubles receiving |y - F x_n| for n = 0..N
+ * For a real-time series pass the previous frame's result as x_inout (and x_ref NULL): the frame is then
+ * initialised from and regularised toward it (Sec. 3.2).
+ * Pointers here may be device pointers or host pointers (pageable or pinned); host buffers are copied through
+ * the context's workspace.  The call returns after the work is queued, except that it waits for the stream when
+ * resid is given or x_inout is host memory.  Errors: EINVAL, ECUDA; EBREAKDOWN when the call waited and CG broke
+ * down (the result is still written). */
+NLINV_API nlinv_status nlinv_reconstruct(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x_ref,
+                               nlinv_c32* x_inout, double* resid);
+
+/* Waits up to timeout_s seconds (< 0: no limit) for the context's queued work.  ETIMEOUT if it is still running,
+ * EBREAKDOWN if a CG breakdown was flagged since the last check (the flag is then cleared), ECUDA on a CUDA
+ * error. */
+NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
+
+/* Kernel launches queued by the last nlinv_reconstruct, nlinv_forward, ... call (the graph's kernel nodes when a
+ * graph was replayed).  -1 for a NULL context. */
+NLINV_API long nlinv_last_launch_count(const nlinv_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed nlinv_create when ctx is NULL).  The string is
+ * owned by the library and stays valid until the next call on the same context. */
+NLINV_API const char* nlinv_last_error(const nlinv_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLINV_H */

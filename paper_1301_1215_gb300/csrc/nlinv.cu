@@ -1,0 +1,680 @@
+// C interface, context and solver driver of the GB300 NLINV library (declared in include/nlinv.h).
+//
+// The driver queues the pass kernels of kernels.cuh on the context's stream:
+//   coil maps      c_j = W^-1 chat_j on Omega                  row ROW_W_IFFT, col COL_IFFT_C
+//   F x            P FFT(M rho c_j)                            col COL_PROD_FFT, row ROW_FFT_P_OUT / ROW_FFT_RESID
+//   DF dx          P FFT(M (drho c_j + rho W^-1 dchat_j))       row ROW_W_IFFT, col COL_IFFT_PROD_FFT, row ROW_FFT_P_OUT
+//   DF^H r         (sum_j conj(c_j) z_j, w FFT(conj(rho) z_j)) row ROW_P_IFFT, col COL_IFFT_ADJ_FFT, row ROW_FFT_W_ADJ
+//   (DF^H DF + alpha) p   the PSF form of Sec. 3.1: row ROW_W_IFFT, col COL_IFFT_PROD_FFT, row ROW_PSF,
+//                         col COL_IFFT_ADJ_FFT, row ROW_FFT_W_NORMAL (+ Re<p, q>)
+//   CG updates     dx += alpha p, r -= alpha q (+ |r|^2); p = r + beta p
+// Each operator application performs the two 2D transforms per operator of Table 1, batched over all coils.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "nlinv.h"
+#include "sizes.cuh"
+
+using nlv::KArgs;
+using nlv::Scalars;
+using nlv::SizeKernels;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ------------------------------------------------------------------------------------------ vector kernels ----
+// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.   n2 = number of complex pairs (float4 accesses).
+__global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, const float4* __restrict__ q4,
+                               float4* __restrict__ r4, float4* __restrict__ dx4, long n2) {
+  const float a = (float)A.sc->alpha;
+  float acc = 0.f;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 p = p4[i], q = q4[i], r = r4[i], d = dx4[i];
+    d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
+    r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
+    dx4[i] = d;
+    r4[i] = r;
+    acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+  }
+  nlv::grid_reduce(acc, A);
+}
+
+// p = r + beta p
+__global__ void cg_dir_kernel(const KArgs A, const float4* __restrict__ r4, float4* __restrict__ p4, long n2) {
+  const float b = (float)A.sc->beta;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 r = r4[i], p = p4[i];
+    p.x = fmaf(b, p.x, r.x); p.y = fmaf(b, p.y, r.y); p.z = fmaf(b, p.z, r.z); p.w = fmaf(b, p.w, r.w);
+    p4[i] = p;
+  }
+}
+
+// x += dx
+__global__ void add_kernel(const float4* __restrict__ d4, float4* __restrict__ x4, long n2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 d = d4[i], x = x4[i];
+    x.x += d.x; x.y += d.y; x.z += d.z; x.w += d.w;
+    x4[i] = x;
+  }
+}
+
+constexpr int kVecThreads = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+// ----------------------------------------------------------------------------------------------- context ----
+struct nlinv_ctx {
+  nlinv_params prm{};
+  int N = 0, J = 0, f = 0, Wc = 0;
+  long plane = 0;             // N*N
+  long vec = 0;               // (1+J)*N*N complex values of an unknown-space vector
+  const SizeKernels* k = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int vec_blocks = 0;         // grid of the vector kernels
+  // workspace (one allocation)
+  void* base = nullptr;
+  float2 *x = nullptr, *xref = nullptr, *y = nullptr, *r0 = nullptr;
+  float2 *r = nullptr, *p = nullptr, *q = nullptr, *dx = nullptr;
+  float2 *T = nullptr, *coil = nullptr, *zsum = nullptr;
+  float2 *twA = nullptr, *twB = nullptr;
+  uint8_t* mask = nullptr;
+  double* partials = nullptr;
+  Scalars* sc = nullptr;
+  // graph of one reconstruction
+  cudaGraphExec_t graph = nullptr;
+  long graph_launches = 0;
+  long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+nlinv_status fail(nlinv_ctx* c, nlinv_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return s;
+}
+
+nlinv_status cuda_fail(nlinv_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, NLINV_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define NLV_TRY(call, where)                           \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+KArgs base_args(const nlinv_ctx* c) {
+  KArgs a{};
+  a.N = c->N;
+  a.J = c->J;
+  a.f = c->f;
+  a.Wc = c->Wc;
+  a.sob_a = (float)c->prm.sobolev_a;
+  a.sob_halfl = (float)(0.5 * c->prm.sobolev_l);
+  const double hl = 0.5 * c->prm.sobolev_l;
+  a.sob_ipow = (hl == std::floor(hl) && hl >= 0 && hl <= 64) ? (int)hl : -1;
+  a.twA = c->twA;
+  a.twB = c->twB;
+  a.partials = c->partials;
+  a.sc = c->sc;
+  a.reduce = nlv::RED_NONE;
+  return a;
+}
+
+int row_blocks(const nlinv_ctx* c, bool with_rho) {
+  const int L = c->k->row_lanes;
+  int b = (c->J * c->N + L - 1) / L;
+  if (with_rho) b += (c->N + L - 1) / L;
+  return b;
+}
+
+int col_blocks(const nlinv_ctx* c) {
+  const int C = c->k->col_lanes;
+  return c->J * ((c->Wc + C - 1) / C);
+}
+
+cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
+  c->launches++;
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, c->stream);
+}
+
+cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
+  const bool rho = (mode == nlv::ROW_FFT_W_ADJ || mode == nlv::ROW_FFT_W_NORMAL || mode == nlv::ROW_FFT_W_RHS);
+  a.nrows = c->J * c->N;
+  a.coil_blocks = row_blocks(c, false);
+  void* args[] = {&a};
+  return launch(c, c->k->row[mode], row_blocks(c, rho), c->k->row_threads, c->k->row_smem, args);
+}
+
+cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
+  a.nrows = c->J;
+  void* args[] = {&a};
+  return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem, args);
+}
+
+// c_j = W^-1 chat_j on Omega, for the coil planes of x (1+J planes).
+cudaError_t q_coils(nlinv_ctx* c, const float2* x) {
+  KArgs a = base_args(c);
+  a.src = x + c->plane;
+  a.dst = c->T;
+  cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
+  if (e != cudaSuccess) return e;
+  a = base_args(c);
+  a.src = c->T;
+  a.dst = c->coil;
+  return col(c, nlv::COL_IFFT_C, a);
+}
+
+// T <- FFT_col(M rho c_j) for rho = plane 0 of x (coil maps already in c->coil)
+cudaError_t q_prod(nlinv_ctx* c, const float2* rho) {
+  KArgs a = base_args(c);
+  a.rho = rho;
+  a.coil = c->coil;
+  a.dst = c->T;
+  return col(c, nlv::COL_PROD_FFT, a);
+}
+
+// T <- FFT_col(M (drho c_j + rho W^-1 dchat_j)) for direction d and linearisation point x
+cudaError_t q_dir(nlinv_ctx* c, const float2* x, const float2* d) {
+  KArgs a = base_args(c);
+  a.src = d + c->plane;
+  a.dst = c->T;
+  cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
+  if (e != cudaSuccess) return e;
+  a = base_args(c);
+  a.src = c->T;
+  a.dst = c->T;
+  a.rho = x;
+  a.drho = d;
+  a.coil = c->coil;
+  return col(c, nlv::COL_IFFT_PROD_FFT, a);
+}
+
+// T <- FFT_col(conj(rho) z_j), zsum_j <- conj(c_j) z_j, with z_j = M FFT^-1_col(T)
+cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
+  KArgs a = base_args(c);
+  a.src = c->T;
+  a.dst = c->T;
+  a.rho = x;
+  a.coil = c->coil;
+  a.zsum = c->zsum;
+  return col(c, nlv::COL_IFFT_ADJ_FFT, a);
+}
+
+// One CG iteration on (DF^H DF + alpha) for linearisation point x: q, alpha, dx, r, beta, p.
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool update_dir) {
+  cudaError_t e = q_dir(c, x, c->p);
+  if (e != cudaSuccess) return e;
+  KArgs a = base_args(c);
+  a.src = c->T;
+  a.dst = c->T;
+  a.mask = c->mask;
+  if ((e = row(c, nlv::ROW_PSF, a)) != cudaSuccess) return e;
+  if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
+  a = base_args(c);
+  a.src = c->T;
+  a.dst = c->q;
+  a.p = c->p;
+  a.zsum = c->zsum;
+  a.alpha = alpha;
+  a.reduce = nlv::RED_PQ;
+  if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
+  a = base_args(c);
+  a.reduce = nlv::RED_RR_UPDATE;
+  const long n2 = c->vec / 2;
+  const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
+  float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
+  {
+    void* args[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
+    if ((e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
+  }
+  if (update_dir) {
+    const float4* rr4 = (const float4*)c->r;
+    float4* pp4 = (float4*)c->p;
+    void* args[] = {&a, &rr4, &pp4, (void*)&n2};
+    if ((e = launch(c, (const void*)cg_dir_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
+cudaError_t q_residual(nlinv_ctx* c, int slot) {
+  cudaError_t e = q_coils(c, c->x);
+  if (e != cudaSuccess) return e;
+  if ((e = q_prod(c, c->x)) != cudaSuccess) return e;
+  KArgs a = base_args(c);
+  a.src = c->T;
+  a.dst = c->r0;
+  a.y = c->y;
+  a.mask = c->mask;
+  a.reduce = nlv::RED_RESID;
+  a.slot = slot;
+  return row(c, nlv::ROW_FFT_RESID, a);
+}
+
+// The whole reconstruction on the workspace buffers (x, xref, y, mask already in place).
+cudaError_t q_reconstruct(nlinv_ctx* c) {
+  const nlinv_params& P = c->prm;
+  double alpha = P.alpha0;
+  cudaError_t e;
+  for (int n = 0; n < P.newton_steps; ++n) {
+    const float al = (float)alpha;
+    if ((e = q_residual(c, n)) != cudaSuccess) return e;
+    // b = DF^H r0 - alpha (x - xref) -> r = p = b, dx = 0, rr = |b|^2
+    KArgs a = base_args(c);
+    a.src = c->r0;
+    a.dst = c->T;
+    a.mask = c->mask;
+    if ((e = row(c, nlv::ROW_P_IFFT, a)) != cudaSuccess) return e;
+    if ((e = q_adj_col(c, c->x)) != cudaSuccess) return e;
+    a = base_args(c);
+    a.src = c->T;
+    a.zsum = c->zsum;
+    a.x = c->x;
+    a.xref = c->xref;
+    a.r = c->r;
+    a.pout = c->p;
+    a.dx = c->dx;
+    a.alpha = al;
+    a.reduce = nlv::RED_RR_INIT;
+    if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
+    for (int i = 0; i < P.cg_iters; ++i)
+      if ((e = q_cg_iter(c, c->x, al, i + 1 < P.cg_iters)) != cudaSuccess) return e;
+    const long n2 = c->vec / 2;
+    const float4* d4 = (const float4*)c->dx;
+    float4* x4 = (float4*)c->x;
+    void* args[] = {&d4, &x4, (void*)&n2};
+    if ((e = launch(c, (const void*)add_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
+    alpha = std::max(alpha * P.alpha_q, P.alpha_min);
+  }
+  return q_residual(c, P.newton_steps);
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+nlinv_status check_dev(nlinv_ctx* c, const void* p, const char* name) {
+  if (!p) return fail(c, NLINV_EINVAL, std::string(name) + " is NULL");
+  if (!is_device_ptr(p)) return fail(c, NLINV_EINVAL, std::string(name) + " must be a device pointer");
+  return NLINV_OK;
+}
+
+nlinv_status validate(const nlinv_params* p, std::string* why) {
+  if (!p) { *why = "params is NULL"; return NLINV_EINVAL; }
+  if (!nlinv_supported_size(p->n)) { *why = "grid side n=" + std::to_string(p->n) + " has no compiled transform"; return NLINV_EINVAL; }
+  if (p->ncoils < 1 || p->ncoils > 64) { *why = "ncoils must be in 1..64"; return NLINV_EINVAL; }
+  if (p->newton_steps < 1 || p->newton_steps > nlv::kMaxNewton) { *why = "newton_steps must be in 1..64"; return NLINV_EINVAL; }
+  if (p->cg_iters < 0 || p->cg_iters > 100000) { *why = "cg_iters must be in 0..100000"; return NLINV_EINVAL; }
+  if (!(p->alpha0 > 0) || !std::isfinite(p->alpha0)) { *why = "alpha0 must be positive"; return NLINV_EINVAL; }
+  if (!(p->alpha_q > 0 && p->alpha_q <= 1)) { *why = "alpha_q must be in (0, 1]"; return NLINV_EINVAL; }
+  if (!(p->alpha_min >= 0) || !std::isfinite(p->alpha_min)) { *why = "alpha_min must be >= 0"; return NLINV_EINVAL; }
+  if (!(p->sobolev_a >= 0) || !std::isfinite(p->sobolev_a)) { *why = "sobolev_a must be >= 0"; return NLINV_EINVAL; }
+  if (!(p->sobolev_l >= 0) || !std::isfinite(p->sobolev_l)) { *why = "sobolev_l must be >= 0"; return NLINV_EINVAL; }
+  if (p->fov < 1 || p->fov > p->n / 2) { *why = "fov must be in 1..n/2"; return NLINV_EINVAL; }
+  return NLINV_OK;
+}
+
+nlinv_status finish_call(nlinv_ctx* c, cudaError_t e, const char* where) {
+  if (e != cudaSuccess) return cuda_fail(c, e, where);
+  return NLINV_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------- C-ABI ----
+extern "C" {
+
+int nlinv_supported_size(int n) { return nlv::find_size(n) != nullptr ? 1 : 0; }
+
+nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils) {
+  if (!p) return NLINV_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->ncoils = ncoils;
+  p->newton_steps = 7;
+  p->cg_iters = 30;
+  p->alpha0 = 1.0;
+  p->alpha_q = 0.5;
+  p->alpha_min = 0.0;
+  p->sobolev_a = 220.0;
+  p->sobolev_l = 32.0;
+  p->fov = n / 4;
+  p->use_graph = 1;
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** out) {
+  nlinv_ctx* c = nullptr;
+  if (!out) return fail(nullptr, NLINV_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (validate(params, &why) != NLINV_OK) return fail(nullptr, NLINV_EINVAL, why);
+  c = new (std::nothrow) nlinv_ctx();
+  if (!c) return fail(nullptr, NLINV_ENOMEM, "host allocation failed");
+  c->prm = *params;
+  c->N = params->n;
+  c->J = params->ncoils;
+  c->f = params->fov;
+  c->Wc = 2 * params->fov;
+  c->plane = (long)c->N * c->N;
+  c->vec = (long)(1 + c->J) * c->plane;
+  c->k = nlv::find_size(c->N);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e); delete c; return NLINV_ECUDA; }
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e); delete c; return NLINV_ECUDA; }
+    c->own_stream = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->vec_blocks = std::max(1, sms) * 4;
+
+  // dynamic shared memory above the 48 KB default
+  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m)
+    if (c->k->row_smem > 48 * 1024)
+      cudaFuncSetAttribute(c->k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->k->row_smem);
+  for (int m = 0; m < nlv::NUM_COL_MODES; ++m)
+    if (c->k->col_smem > 48 * 1024)
+      cudaFuncSetAttribute(c->k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->k->col_smem);
+
+  // workspace layout
+  const size_t cplx = sizeof(float2);
+  const size_t vecb = align_up(c->vec * cplx, 256), datab = align_up((size_t)c->J * c->plane * cplx, 256);
+  const size_t Tb = align_up((size_t)c->J * c->N * c->Wc * cplx, 256);
+  const size_t cb = align_up((size_t)c->J * c->Wc * c->Wc * cplx, 256);
+  const size_t twb = align_up((size_t)c->N * cplx, 256);
+  const size_t maskb = align_up((size_t)c->plane, 256);
+  const int max_blocks = std::max(row_blocks(c, true), c->vec_blocks);
+  const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
+  const size_t scb = align_up(sizeof(Scalars), 256);
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + maskb + partb + scb;
+  e = cudaMalloc(&c->base, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_create_error = "cudaMalloc of " + std::to_string(total) + " bytes failed: " + cudaGetErrorString(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NLINV_ENOMEM;
+  }
+  char* b = (char*)c->base;
+  auto take = [&](size_t n) { char* r = b; b += n; return r; };
+  c->x = (float2*)take(vecb);
+  c->xref = (float2*)take(vecb);
+  c->r = (float2*)take(vecb);
+  c->p = (float2*)take(vecb);
+  c->q = (float2*)take(vecb);
+  c->dx = (float2*)take(vecb);
+  c->y = (float2*)take(datab);
+  c->r0 = (float2*)take(datab);
+  c->T = (float2*)take(Tb);
+  c->coil = (float2*)take(cb);
+  c->zsum = (float2*)take(cb);
+  c->twA = (float2*)take(twb);
+  c->twB = (float2*)take(twb);
+  c->mask = (uint8_t*)take(maskb);
+  c->partials = (double*)take(partb);
+  c->sc = (Scalars*)take(scb);
+
+  // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
+  const int N = c->N, N1 = c->k->N1, N2 = c->k->N2;
+  std::vector<float2> ta(N), tb(N);
+  auto tw = [N](long m) {
+    m %= N;
+    const double t = 2.0 * 3.14159265358979323846 * (double)m / (double)N;
+    return make_float2((float)std::cos(t), (float)-std::sin(t));
+  };
+  for (int k2 = 0; k2 < N2; ++k2)
+    for (int a = 0; a < N1; ++a) ta[k2 * N1 + a] = tw((long)a * k2);
+  for (int k2 = 0; k2 < N1; ++k2)
+    for (int a = 0; a < N2; ++a) tb[k2 * N2 + a] = tw((long)a * k2);
+  e = cudaMemset(c->base, 0, total);
+  if (e == cudaSuccess) e = cudaMemcpy(c->twA, ta.data(), N * cplx, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->twB, tb.data(), N * cplx, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("context set-up: ") + cudaGetErrorString(e);
+    cudaFree(c->base);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NLINV_ECUDA;
+  }
+  *out = c;
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_destroy(nlinv_ctx* c) {
+  if (!c) return NLINV_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  cudaFree(c->base);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_forward(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask, nlinv_c32* y_out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, x, "x")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, y_out, "y_out"))) return s;
+  c->launches = 0;
+  const float2* xv = (const float2*)x;
+  cudaError_t e = q_coils(c, xv);
+  if (e == cudaSuccess) e = q_prod(c, xv);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = c->T;
+    a.dst = (float2*)y_out;
+    a.mask = mask;
+    e = row(c, nlv::ROW_FFT_P_OUT, a);
+  }
+  return finish_call(c, e, "nlinv_forward");
+}
+
+nlinv_status nlinv_derivative(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* dx,
+                              nlinv_c32* out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, x, "x")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, dx, "dx")) ||
+      (s = check_dev(c, out, "out")))
+    return s;
+  c->launches = 0;
+  cudaError_t e = q_coils(c, (const float2*)x);
+  if (e == cudaSuccess) e = q_dir(c, (const float2*)x, (const float2*)dx);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = c->T;
+    a.dst = (float2*)out;
+    a.mask = mask;
+    e = row(c, nlv::ROW_FFT_P_OUT, a);
+  }
+  return finish_call(c, e, "nlinv_derivative");
+}
+
+nlinv_status nlinv_adjoint(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* r,
+                           nlinv_c32* out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, x, "x")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, r, "r")) ||
+      (s = check_dev(c, out, "out")))
+    return s;
+  c->launches = 0;
+  cudaError_t e = q_coils(c, (const float2*)x);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = (const float2*)r;
+    a.dst = c->T;
+    a.mask = mask;
+    e = row(c, nlv::ROW_P_IFFT, a);
+  }
+  if (e == cudaSuccess) e = q_adj_col(c, (const float2*)x);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = c->T;
+    a.dst = (float2*)out;
+    a.zsum = c->zsum;
+    e = row(c, nlv::ROW_FFT_W_ADJ, a);
+  }
+  return finish_call(c, e, "nlinv_adjoint");
+}
+
+nlinv_status nlinv_normal(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* d, double alpha,
+                          nlinv_c32* out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, x, "x")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, d, "d")) ||
+      (s = check_dev(c, out, "out")))
+    return s;
+  if (!std::isfinite(alpha)) return fail(c, NLINV_EINVAL, "alpha must be finite");
+  c->launches = 0;
+  const float2* xv = (const float2*)x;
+  cudaError_t e = q_coils(c, xv);
+  if (e == cudaSuccess) e = q_dir(c, xv, (const float2*)d);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = c->T;
+    a.dst = c->T;
+    a.mask = mask;
+    e = row(c, nlv::ROW_PSF, a);
+  }
+  if (e == cudaSuccess) e = q_adj_col(c, xv);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.src = c->T;
+    a.dst = (float2*)out;
+    a.p = (const float2*)d;
+    a.zsum = c->zsum;
+    a.alpha = (float)alpha;
+    a.reduce = nlv::RED_NONE;
+    e = row(c, nlv::ROW_FFT_W_NORMAL, a);
+  }
+  return finish_call(c, e, "nlinv_normal");
+}
+
+nlinv_status nlinv_simulate(nlinv_ctx* c, const nlinv_c32* rho, const nlinv_c32* coil_img, const uint8_t* mask,
+                            nlinv_c32* y_out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, rho, "rho")) || (s = check_dev(c, coil_img, "coil_img")) ||
+      (s = check_dev(c, mask, "mask")) || (s = check_dev(c, y_out, "y_out")))
+    return s;
+  c->launches = 0;
+  KArgs a = base_args(c);
+  a.rho = (const float2*)rho;
+  a.cimg = (const float2*)coil_img;
+  a.dst = c->T;
+  cudaError_t e = col(c, nlv::COL_SIM_FFT, a);
+  if (e == cudaSuccess) {
+    a = base_args(c);
+    a.src = c->T;
+    a.dst = (float2*)y_out;
+    a.mask = mask;
+    e = row(c, nlv::ROW_FFT_P_OUT, a);
+  }
+  return finish_call(c, e, "nlinv_simulate");
+}
+
+nlinv_status nlinv_reconstruct(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x_ref,
+                               nlinv_c32* x_inout, double* resid) {
+  if (!c) return NLINV_EINVAL;
+  if (!y || !mask || !x_inout) return fail(c, NLINV_EINVAL, "y, mask and x_inout must not be NULL");
+  const size_t vb = c->vec * sizeof(float2), db = (size_t)c->J * c->plane * sizeof(float2);
+  const bool host_x = !is_device_ptr(x_inout);
+  NLV_TRY(cudaMemcpyAsync(c->y, y, db, cudaMemcpyDefault, c->stream), "copy y");
+  NLV_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->plane, cudaMemcpyDefault, c->stream), "copy mask");
+  NLV_TRY(cudaMemcpyAsync(c->x, x_inout, vb, cudaMemcpyDefault, c->stream), "copy x");
+  NLV_TRY(cudaMemcpyAsync(c->xref, x_ref ? (const void*)x_ref : (const void*)c->x, vb, cudaMemcpyDefault, c->stream),
+          "copy x_ref");
+  if (c->prm.use_graph) {
+    if (!c->graph) {
+      cudaGraph_t g = nullptr;
+      c->launches = 0;
+      NLV_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cudaError_t e = q_reconstruct(c);
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e != cudaSuccess ? e : e2, "capture reconstruction");
+      }
+      e = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(c, e, "instantiate graph"); }
+      c->graph_launches = c->launches;
+    }
+    NLV_TRY(cudaGraphLaunch(c->graph, c->stream), "graph launch");
+    c->launches = c->graph_launches;
+  } else {
+    c->launches = 0;
+    NLV_TRY(q_reconstruct(c), "reconstruction");
+  }
+  NLV_TRY(cudaMemcpyAsync(x_inout, c->x, vb, cudaMemcpyDefault, c->stream), "copy x out");
+  if (resid || host_x) {
+    Scalars hs{};
+    NLV_TRY(cudaMemcpyAsync(&hs, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream), "read scalars");
+    NLV_TRY(cudaStreamSynchronize(c->stream), "synchronize");
+    if (resid)
+      for (int n = 0; n <= c->prm.newton_steps; ++n) resid[n] = hs.resid[n];
+    if (hs.flags & 1) {
+      int zero = 0;
+      cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(c, NLINV_EBREAKDOWN, "CG breakdown: Re<p, A p> <= 0 or not finite");
+    }
+  }
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_wait(nlinv_ctx* c, double timeout_s) {
+  if (!c) return NLINV_EINVAL;
+  cudaEvent_t ev;
+  NLV_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+  cudaError_t e = cudaEventRecord(ev, c->stream);
+  if (e != cudaSuccess) { cudaEventDestroy(ev); return cuda_fail(c, e, "event record"); }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    e = cudaEventQuery(ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) { cudaEventDestroy(ev); return cuda_fail(c, e, "wait"); }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s >= 0 && el > timeout_s) {
+      cudaEventDestroy(ev);
+      return fail(c, NLINV_ETIMEOUT, "queued work did not finish within the time limit");
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  cudaEventDestroy(ev);
+  int flags = 0;
+  NLV_TRY(cudaMemcpy(&flags, &c->sc->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+  if (flags & 1) {
+    int zero = 0;
+    NLV_TRY(cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
+    return fail(c, NLINV_EBREAKDOWN, "CG breakdown: Re<p, A p> <= 0 or not finite");
+  }
+  return NLINV_OK;
+}
+
+long nlinv_last_launch_count(const nlinv_ctx* c) { return c ? c->launches : -1; }
+
+const char* nlinv_last_error(const nlinv_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// Grid sides with compiled transforms and their four-step splits N = N1 * N2.  Each sizes_*.cu file instantiates
+// the pass kernels of a few sides so that they compile in parallel.
+#pragma once
+#include "kernels.cuh"
+
+namespace nlv {
+
+// Lookup functions defined by the sizes_*.cu files: the kernel table of side n, or nullptr if that file does not
+// hold n.
+const SizeKernels* sizes_small(int n);
+const SizeKernels* sizes_mid(int n);
+const SizeKernels* sizes_256(int n);
+const SizeKernels* sizes_384(int n);
+const SizeKernels* sizes_512(int n);
+
+inline const SizeKernels* find_size(int n) {
+  const SizeKernels* s = nullptr;
+  if (!s) s = sizes_small(n);
+  if (!s) s = sizes_mid(n);
+  if (!s) s = sizes_256(n);
+  if (!s) s = sizes_384(n);
+  if (!s) s = sizes_512(n);
+  return s;
+}
+
+}  // namespace nlv
+
+#define NLV_SIZE_CASE(n, a, b)                                      \
+  case n: {                                                         \
+    static const ::nlv::SizeKernels k = ::nlv::make_size_kernels<a, b>(); \
+    return &k;                                                      \
+  }

@@ -1,0 +1,9 @@
+#include "sizes.cuh"
+namespace nlv {
+const SizeKernels* sizes_512(int n) {
+  switch (n) {
+    NLV_SIZE_CASE(512, 16, 32)
+    default: return nullptr;
+  }
+}
+}  // namespace nlv

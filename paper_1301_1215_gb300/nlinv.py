@@ -1,0 +1,202 @@
+"""PyTorch-facing binding of libnlinv.so: argument marshalling only.
+
+Every method hands device pointers of complex64 / uint8 tensors to the C interface of include/nlinv.h; the
+operators F, DF, DF^H, the normal operator of Eq. 3 and the whole Gauss-Newton reconstruction run in the
+library's CUDA kernels.  There is no CPU fallback: without the built library or a GPU the calls raise.
+
+Tensor layouts follow the C interface: a plane is an (n, n) complex64 tensor in natural FFT order; the unknown
+x = (rho, chat_1 .. chat_J) has shape (1 + J, n, n); data-space arrays have shape (J, n, n); the sampling pattern
+is an (n, n) uint8 tensor.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+
+__all__ = ["Nlinv", "supported_size", "NlinvError"]
+
+NlinvError = _lib.NlinvError
+
+
+def supported_size(n: int) -> bool:
+    """True if the library has a compiled transform for grid side n."""
+    return bool(_lib.load().nlinv_supported_size(int(n)))
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Nlinv:
+    """One NLINV context: grid side ``n``, ``ncoils`` coils and the solver schedule of Eq. 3.
+
+    The context owns a CUDA stream; each call orders itself after the caller's current stream and makes the
+    current stream wait for it, so results can be used right away on the current stream.
+    """
+
+    def __init__(self, n: int, ncoils: int, *, newton_steps: int = 7, cg_iters: int = 30, alpha0: float = 1.0,
+                 alpha_q: float = 0.5, alpha_min: float = 0.0, sobolev_a: float = 220.0, sobolev_l: float = 32.0,
+                 fov: Optional[int] = None, use_graph: bool = True, device=None):
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("Nlinv needs a CUDA device; there is no CPU implementation")
+        self.device = torch.device(device if device is not None else "cuda", )
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        p = _lib.Params()
+        lib.nlinv_default_params(C.byref(p), int(n), int(ncoils))
+        p.newton_steps, p.cg_iters = int(newton_steps), int(cg_iters)
+        p.alpha0, p.alpha_q, p.alpha_min = float(alpha0), float(alpha_q), float(alpha_min)
+        p.sobolev_a, p.sobolev_l = float(sobolev_a), float(sobolev_l)
+        p.fov = int(n // 4 if fov is None else fov)
+        p.use_graph = 1 if use_graph else 0
+        self.params = p
+        self.n, self.ncoils = int(n), int(ncoils)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(self.device)
+            _lib.check(lib.nlinv_create(C.byref(p), C.c_void_p(self.stream.cuda_stream), C.byref(self._h)), None)
+        self._lib = lib
+
+    # ------------------------------------------------------------------------------------------ helpers ----
+    def close(self) -> None:
+        if self._h:
+            self._lib.nlinv_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, status: int) -> None:
+        _lib.check(status, self._h)
+
+    def _shape_x(self):
+        return (1 + self.ncoils, self.n, self.n)
+
+    def _shape_y(self):
+        return (self.ncoils, self.n, self.n)
+
+    def _dev(self, t: torch.Tensor, shape: Sequence[int], dtype, name: str) -> torch.Tensor:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch.Tensor")
+        if t.device != self.device:
+            raise ValueError(f"{name} must be on {self.device}, got {t.device}")
+        if t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+        return t.contiguous()
+
+    def _x(self, t, name="x"):
+        return self._dev(t, self._shape_x(), torch.complex64, name)
+
+    def _y(self, t, name="y"):
+        return self._dev(t, self._shape_y(), torch.complex64, name)
+
+    def _m(self, t, name="mask"):
+        return self._dev(t, (self.n, self.n), torch.uint8, name)
+
+    def _begin(self):
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def _end(self):
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
+    # ---------------------------------------------------------------------------------------- operators ----
+    def forward(self, x: torch.Tensor, mask: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """F x (Eq. 2): P FFT(M rho c_j) with c_j = W^-1 chat_j; shape (J, n, n)."""
+        x, mask = self._x(x), self._m(mask)
+        out = torch.empty(self._shape_y(), dtype=torch.complex64, device=self.device) if out is None else self._y(out, "out")
+        self._begin()
+        self._check(self._lib.nlinv_forward(self._h, _ptr(x), _ptr(mask), _ptr(out)))
+        self._end()
+        return out
+
+    def derivative(self, x, mask, dx, out=None) -> torch.Tensor:
+        """DF_x dx: P FFT(M (drho c_j + rho W^-1 dchat_j)); shape (J, n, n)."""
+        x, mask, dx = self._x(x), self._m(mask), self._x(dx, "dx")
+        out = torch.empty(self._shape_y(), dtype=torch.complex64, device=self.device) if out is None else self._y(out, "out")
+        self._begin()
+        self._check(self._lib.nlinv_derivative(self._h, _ptr(x), _ptr(mask), _ptr(dx), _ptr(out)))
+        self._end()
+        return out
+
+    def adjoint(self, x, mask, r, out=None) -> torch.Tensor:
+        """DF_x^H r: (sum_j conj(c_j) z_j, w FFT(conj(rho) z_j)) with z_j = M FFT^-1(P r_j); shape (1+J, n, n)."""
+        x, mask, r = self._x(x), self._m(mask), self._y(r, "r")
+        out = torch.empty(self._shape_x(), dtype=torch.complex64, device=self.device) if out is None else self._x(out, "out")
+        self._begin()
+        self._check(self._lib.nlinv_adjoint(self._h, _ptr(x), _ptr(mask), _ptr(r), _ptr(out)))
+        self._end()
+        return out
+
+    def normal(self, x, mask, d, alpha: float, out=None) -> torch.Tensor:
+        """(DF_x^H DF_x + alpha I) d, the left-hand side of Eq. 3; shape (1+J, n, n)."""
+        x, mask, d = self._x(x), self._m(mask), self._x(d, "d")
+        out = torch.empty(self._shape_x(), dtype=torch.complex64, device=self.device) if out is None else self._x(out, "out")
+        self._begin()
+        self._check(self._lib.nlinv_normal(self._h, _ptr(x), _ptr(mask), _ptr(d), float(alpha), _ptr(out)))
+        self._end()
+        return out
+
+    def simulate(self, rho, coil_img, mask, out=None) -> torch.Tensor:
+        """Gridded signal-equation data (Eq. 1) for image-domain coils: P FFT(M rho c_j); shape (J, n, n)."""
+        rho = self._dev(rho, (self.n, self.n), torch.complex64, "rho")
+        coil_img, mask = self._y(coil_img, "coil_img"), self._m(mask)
+        out = torch.empty(self._shape_y(), dtype=torch.complex64, device=self.device) if out is None else self._y(out, "out")
+        self._begin()
+        self._check(self._lib.nlinv_simulate(self._h, _ptr(rho), _ptr(coil_img), _ptr(mask), _ptr(out)))
+        self._end()
+        return out
+
+    # ---------------------------------------------------------------------------------- reconstruction ----
+    def reconstruct(self, y: torch.Tensor, mask: torch.Tensor, x0: Optional[torch.Tensor] = None,
+                    x_ref: Optional[torch.Tensor] = None, resid: bool = False):
+        """Gauss-Newton reconstruction (Eq. 3) from x0 (default: rho = 1, chat = 0), regularised toward x_ref
+        (default: x0).  Returns x_N, or (x_N, residual norms |y - F x_n| for n = 0..N) when ``resid``."""
+        y, mask = self._y(y), self._m(mask)
+        if x0 is None:
+            x = torch.zeros(self._shape_x(), dtype=torch.complex64, device=self.device)
+            x[0] = 1.0
+        else:
+            x = self._x(x0, "x0").clone()
+        xr = None if x_ref is None else self._x(x_ref, "x_ref")
+        return self._run(y, mask, xr, x, resid)
+
+    def reconstruct_inplace(self, y, mask, x_inout, x_ref=None, resid: bool = False):
+        """As :meth:`reconstruct`, writing x_N over ``x_inout``.  Any argument may be a CPU tensor: host buffers
+        are copied through the library's workspace (the call then waits for the result)."""
+        return self._run(y, mask, x_ref, x_inout, resid)
+
+    def _run(self, y, mask, xr, x, resid):
+        nres = self.params.newton_steps + 1
+        buf = (C.c_double * nres)() if resid else None
+        self._begin()
+        self._check(self._lib.nlinv_reconstruct(self._h, _ptr(y), _ptr(mask), _ptr(xr), _ptr(x),
+                                                buf if resid else None))
+        self._end()
+        if resid:
+            return x, [float(v) for v in buf]
+        return x
+
+    def wait(self, timeout_s: float = -1.0) -> None:
+        """Waits for the context's queued work (raises NlinvError with ETIMEOUT or EBREAKDOWN)."""
+        self._check(self._lib.nlinv_wait(self._h, float(timeout_s)))
+
+    @property
+    def last_launch_count(self) -> int:
+        """Kernel launches queued by the last call (kernel nodes of the graph when one was replayed)."""
+        return int(self._lib.nlinv_last_launch_count(self._h))

@@ -1,0 +1,99 @@
+"""Host-side checks of the C interface: the library builds, loads and exports every declared entry point, and
+argument validation answers before any CUDA call.  No GPU is used."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from tests.helpers import ensure_built
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = ensure_built()
+    from paper_1301_1215_gb300 import _lib
+    return _lib.load(path)
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"NLINV_API\s+[\w\s\*]+?\b(nlinv_\w+)\s*\(", text)
+    return names
+
+
+def test_every_declared_function_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), f"{n} is declared in include/ but not exported"
+
+
+def test_binding_covers_every_declared_function():
+    from paper_1301_1215_gb300 import _lib
+    assert set(declared_functions()) == set(_lib.SIGNATURES)
+
+
+def test_supported_sizes(lib):
+    for n in (16, 32, 48, 64, 80, 96, 128, 160, 192, 256, 320, 384, 512):
+        assert lib.nlinv_supported_size(n) == 1
+    for n in (0, 8, 100, 1000, 1024, -64):
+        assert lib.nlinv_supported_size(n) == 0
+
+
+def test_default_params(lib):
+    from paper_1301_1215_gb300 import _lib
+    p = _lib.Params()
+    assert lib.nlinv_default_params(C.byref(p), 384, 10) == _lib.OK
+    assert (p.n, p.ncoils, p.newton_steps, p.cg_iters, p.fov, p.use_graph) == (384, 10, 7, 30, 96, 1)
+    assert (p.alpha0, p.alpha_q, p.alpha_min, p.sobolev_a, p.sobolev_l) == (1.0, 0.5, 0.0, 220.0, 32.0)
+    assert lib.nlinv_default_params(None, 64, 4) == _lib.EINVAL
+
+
+@pytest.mark.parametrize("field,value", [("n", 100), ("ncoils", 0), ("newton_steps", 0), ("newton_steps", 65),
+                                         ("cg_iters", -1), ("alpha0", 0.0), ("alpha_q", 1.5), ("alpha_min", -1.0),
+                                         ("sobolev_a", -1.0), ("fov", 0), ("fov", 33)])
+def test_create_rejects_bad_params_before_touching_cuda(lib, field, value):
+    from paper_1301_1215_gb300 import _lib
+    p = _lib.Params()
+    lib.nlinv_default_params(C.byref(p), 64, 4)
+    setattr(p, field, value)
+    h = C.c_void_p()
+    assert lib.nlinv_create(C.byref(p), None, C.byref(h)) == _lib.EINVAL
+    assert not h.value
+    assert lib.nlinv_last_error(None)
+
+
+def test_null_context_is_rejected(lib):
+    from paper_1301_1215_gb300 import _lib
+    assert lib.nlinv_forward(None, None, None, None) == _lib.EINVAL
+    assert lib.nlinv_reconstruct(None, None, None, None, None, None) == _lib.EINVAL
+    assert lib.nlinv_wait(None, 0.0) == _lib.EINVAL
+    assert lib.nlinv_destroy(None) == _lib.OK
+    assert lib.nlinv_last_launch_count(None) == -1
+
+
+def test_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1301_1215_gb300 import _lib
+    p = _lib.Params()
+    lib.nlinv_default_params(C.byref(p), 64, 4)
+    h = C.c_void_p()
+    assert lib.nlinv_create(C.byref(p), None, C.byref(h)) == _lib.ECUDA
+    assert b"cuda" in lib.nlinv_last_error(None).lower()
+
+
+def test_binding_refuses_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    with pytest.raises(RuntimeError):
+        Nlinv(64, 4)

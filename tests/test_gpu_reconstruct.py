@@ -1,0 +1,145 @@
+"""GPU parity of the whole Gauss-Newton reconstruction (Eq. 3 with CG) against the oracle on the seeded
+workloads, plus the real-time series, graph replay, host buffers and the host-visible failure paths.
+
+Bar: final x within relative L2 1e-3 of the oracle; residual norms within 1e-4."""
+import numpy as np
+import pytest
+
+import oracle.nlinv_oracle as O
+from paper_1301_1215_gb300 import synth
+from tests.helpers import ensure_built, noisy_data, rel
+
+pytestmark = pytest.mark.gpu
+TOL_X = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    ensure_built()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+def _t(torch, a):
+    if a.dtype == np.uint8:
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return torch.from_numpy(np.ascontiguousarray(a.astype(np.complex64))).cuda()
+
+
+def _compare(torch, n, J, spokes, newton, cg, seed):
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    s, fr, y = noisy_data(n, J, spokes, seed)
+    y = y.astype(np.complex64).astype(np.complex128)
+    x0 = synth.initial_guess(n, J)
+    xo, ro = O.irgnm(s, fr.mask, y, x0, None, newton, cg)
+    with Nlinv(n, J, newton_steps=newton, cg_iters=cg) as ctx:
+        xg, rg = ctx.reconstruct(_t(torch, y), _t(torch, fr.mask), _t(torch, x0), resid=True)
+        xg = xg.cpu().numpy()
+    assert rel(xg, xo) < TOL_X
+    assert rel(xg[0], xo[0]) < TOL_X
+    assert np.allclose(rg, ro, rtol=1e-4, atol=0)
+    return xg
+
+
+def test_single_frame_64(torch_cuda):
+    _compare(torch_cuda, 64, 4, 16, 7, 30, seed=1001)
+
+
+def test_single_frame_256(torch_cuda):
+    _compare(torch_cuda, 256, 8, 25, 8, 40, seed=1002)
+
+
+def test_realtime_frame_384(torch_cuda):
+    _compare(torch_cuda, 384, 10, 13, 7, 30, seed=1003)
+
+
+def test_graph_and_kernel_by_kernel_agree_bitwise(torch_cuda):
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J = 64, 4
+    s, fr, y = noisy_data(n, J, 16, 11)
+    outs = []
+    for g in (True, False, True):
+        with Nlinv(n, J, newton_steps=3, cg_iters=8, use_graph=g) as ctx:
+            outs.append(ctx.reconstruct(_t(torch, y), _t(torch, fr.mask)).cpu().numpy())
+            if g:
+                outs.append(ctx.reconstruct(_t(torch, y), _t(torch, fr.mask)).cpu().numpy())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_realtime_series_matches_oracle(torch_cuda):
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J, spokes, frames = 64, 4, 9, 3
+    datas = [noisy_data(n, J, spokes, 21, frame=k) for k in range(frames)]
+    s = datas[0][0]
+    ys = [d[2].astype(np.complex64).astype(np.complex128) for d in datas]
+    masks = [d[1].mask for d in datas]
+    ref = O.realtime_series(s, masks, ys, synth.initial_guess(n, J), 4, 15)
+    with Nlinv(n, J, newton_steps=4, cg_iters=15) as ctx:
+        x = _t(torch, synth.initial_guess(n, J))
+        for k in range(frames):
+            ctx.reconstruct_inplace(_t(torch, ys[k]), _t(torch, masks[k]), x)
+            assert rel(x.cpu().numpy(), ref[k]) < TOL_X
+
+
+def test_host_buffers_give_the_device_result(torch_cuda):
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J = 64, 4
+    s, fr, y = noisy_data(n, J, 16, 13)
+    x0 = synth.initial_guess(n, J)
+    with Nlinv(n, J, newton_steps=3, cg_iters=10) as ctx:
+        xd = ctx.reconstruct(_t(torch, y), _t(torch, fr.mask), _t(torch, x0)).cpu().numpy()
+        yh = torch.from_numpy(y.astype(np.complex64)).pin_memory()
+        mh = torch.from_numpy(fr.mask)
+        xh = torch.from_numpy(x0.astype(np.complex64))          # pageable
+        _, res = ctx.reconstruct_inplace(yh, mh, xh, resid=True)
+        assert np.array_equal(xh.numpy(), xd)
+        assert len(res) == 4 and all(np.isfinite(res))
+
+
+def test_zero_data_at_start_value_stays_put(torch_cuda):
+    # y = F(x0) = 0 for chat = 0: the right-hand side vanishes and every CG step is empty
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J = 32, 2
+    x0 = synth.initial_guess(n, J)
+    with Nlinv(n, J, newton_steps=2, cg_iters=5) as ctx:
+        x, res = ctx.reconstruct(_t(torch, np.zeros((J, n, n), complex)), _t(torch, synth.radial_mask(n, 5)),
+                                 _t(torch, x0), resid=True)
+        ctx.wait(-1)
+    assert np.array_equal(x.cpu().numpy(), x0.astype(np.complex64)) and res == [0.0, 0.0, 0.0]
+
+
+def test_nan_data_reports_breakdown(torch_cuda):
+    torch = torch_cuda
+    from paper_1301_1215_gb300 import _lib
+    from paper_1301_1215_gb300.nlinv import Nlinv, NlinvError
+    n, J = 32, 2
+    y = np.full((J, n, n), np.nan, complex)
+    with Nlinv(n, J, newton_steps=1, cg_iters=2) as ctx:
+        with pytest.raises(NlinvError) as ei:
+            ctx.reconstruct(_t(torch, y), _t(torch, np.ones((n, n), np.uint8)), resid=True)
+        assert ei.value.status == _lib.EBREAKDOWN
+        ctx.wait(-1)       # the flag was cleared by the failing call
+
+
+def test_wait_deadline(torch_cuda):
+    torch = torch_cuda
+    from paper_1301_1215_gb300 import _lib
+    from paper_1301_1215_gb300.nlinv import Nlinv, NlinvError
+    n, J = 384, 10
+    s, fr, y = noisy_data(n, J, 13, 1003)
+    with Nlinv(n, J, newton_steps=7, cg_iters=30) as ctx:
+        ty, tm = _t(torch, y), _t(torch, fr.mask)
+        x = ctx.reconstruct(ty, tm)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            x = ctx.reconstruct(ty, tm)
+        with pytest.raises(NlinvError) as ei:
+            ctx.wait(0.0)
+        assert ei.value.status == _lib.ETIMEOUT
+        ctx.wait(-1)
