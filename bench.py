@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the NLINV hot path on one GB300: the real-time radial series of Sec. 3.2.
+
+Workload: 384 x 384 grid (192 x 192 image, 2x oversampled), 10 virtual coils, 13 radial spokes per frame rotated by
+k * 2 pi / 65 from frame to frame, 7 Gauss-Newton steps x 30 CG iterations per frame, each frame initialised from
+and regularised toward the previous one.  One step = one frame reconstruction (every row of the hot path).
+Inputs are synthetic (seeded phantom, Gaussian coil maps, radial masks, 30 dB noise) and resident in HBM before
+the timed region; L2 is flushed before every frame.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead, on bounded samples.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NLINV frames/s and p99 frame latency (384^2, 10 coils); operator % HBM roofline"
+WORKLOAD = "realtime_384"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=195)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1301_1215_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi clock and throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------- workload ----
+def build_series(torch, ctx, W, frames, dev):
+    """Seeded truth (static object), per-frame radial masks and noisy data y_k = P FFT(M rho c_j) + noise,
+    generated on the device with the library's own simulation kernel."""
+    import numpy as np
+    from paper_1301_1215_gb300 import synth
+    fr = synth.make_frame(W.n, W.ncoils, W.spokes, seed=W.seed)
+    rho = torch.from_numpy(fr.rho.astype(np.complex64)).to(dev)
+    coils = torch.from_numpy(fr.coils.astype(np.complex64)).to(dev)
+    masks = torch.stack([torch.from_numpy(synth.radial_mask(W.n, W.spokes, synth.frame_rotation(k, W.spokes)))
+                         for k in range(frames)]).to(dev)
+    ys = torch.empty((frames, W.ncoils, W.n, W.n), dtype=torch.complex64, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.seed)
+    sigma = None
+    for k in range(frames):
+        ctx.simulate(rho, coils, masks[k], out=ys[k])
+        if sigma is None:
+            npts = float(masks[k].sum().item()) * W.ncoils
+            power = float((ys[k].abs() ** 2).sum().item()) / npts
+            sigma = synth.noise_sigma(power, W.snr_db)
+        noise = torch.randn((W.ncoils, W.n, W.n, 2), generator=gen, device=dev) * (sigma * 0.5 ** 0.5)
+        ys[k] += torch.view_as_complex(noise) * masks[k]
+    torch.cuda.synchronize()
+    return ys, masks
+
+
+def cg_bytes(n: int, J: int, fov: int):
+    """Algorithmic bytes per launch of the kernels of one CG iteration: every input read once and every output
+    written once (U = one complex64 plane, compact Omega columns Wc = 2 fov)."""
+    U = n * n * 8
+    h = (2 * fov) / n                 # fraction of a plane kept as Omega columns
+    q = h * h                         # fraction kept as Omega
+    mask = n * n
+    return {
+        "row W^-1": J * U * (1 + h),
+        "col W^-1/C/FFT": J * U * (h + q + h) + 2 * q * U,
+        "row PSF": J * U * 2 * h + mask,
+        "col FFT^-1/C^H/FFT": J * U * (h + q + h + q) + q * U,
+        "row W^-H+alpha p": J * U * (h + q) + 2 * (1 + J) * U,
+        "cg step": 6 * (1 + J) * U,
+        "cg direction": 3 * (1 + J) * U,
+    }
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_1301_1215_gb300 import synth
+    from paper_1301_1215_gb300.build import build
+    from paper_1301_1215_gb300.nlinv import Nlinv
+
+    build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    W = synth.WORKLOADS[WORKLOAD]
+    K, Wm = args.steps, args.warmup
+    frames = K + Wm
+    ctx = Nlinv(W.n, W.ncoils, newton_steps=W.newton_steps, cg_iters=W.cg_iters, alpha0=W.alpha0,
+                alpha_q=W.alpha_q, sobolev_a=W.sobolev_a, sobolev_l=W.sobolev_l, use_graph=True, device=dev)
+    ys, masks = build_series(torch, ctx, W, frames, dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
+    x = torch.zeros((1 + W.ncoils, W.n, W.n), dtype=torch.complex64, device=dev)
+    x[0] = 1.0
+
+    for k in range(Wm):
+        ctx.reconstruct_inplace(ys[k], masks[k], x)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    launches = 0
+    for i in range(K):
+        k = Wm + i
+        flush.zero_()
+        ctx.stream.wait_stream(torch.cuda.current_stream(dev))
+        starts[i].record(ctx.stream)
+        ctx.reconstruct_inplace(ys[k], masks[k], x)
+        ends[i].record(ctx.stream)
+        launches += ctx.last_launch_count
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    frame_ms = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = sum(frame_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K / (total_ms / 1e3)
+    p50 = frame_ms[len(frame_ms) // 2]
+    p99 = frame_ms[min(len(frame_ms) - 1, int(round(0.99 * (len(frame_ms) - 1))))]
+    finite = bool(torch.isfinite(torch.view_as_real(x)).all().item())
+
+    # per-kernel CUDA-event durations of the CG iteration on the same state (the roofline's dominant kernel)
+    prof = ctx.profile_cg(reps=20)
+    algo = cg_bytes(W.n, W.ncoils, W.fov)
+    top = max(prof, key=prof.get)
+    hbm, src = peaks()
+    achieved = algo[top] / (prof[top] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("csrc_digest") == csrc_digest() and top in tj.get("kernels", {}):
+            traffic = tj["kernels"][top]
+    kernels = {k: {"ms": round(v, 5), "algo_bytes": int(algo[k]),
+                   "gbs": round(algo[k] / (v * 1e-3) / 1e9, 1)} for k, v in prof.items()}
+
+    # end to end through the C interface with host buffers: pinned y and mask in, x in and out every frame
+    e2e = None
+    if not args.no_e2e:
+        R = min(8, frames)
+        yh = [ys[k].cpu().pin_memory() for k in range(R)]
+        mh = [masks[k].cpu().pin_memory() for k in range(R)]
+        xh = x.cpu().pin_memory()
+        ctx.reconstruct_inplace(yh[0], mh[0], xh)
+        tot = 0.0
+        for i in range(K):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.reconstruct_inplace(yh[i % R], mh[i % R], xh)   # returns after the copy back to host memory
+            tot += time.perf_counter() - t0
+        bi = yh[0].numel() * 8 + mh[0].numel() + xh.numel() * 8
+        e2e = {"value": round(world * K / tot, 3), "unit": "frames/s", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(xh.numel() * 8)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64 (f32 complex; f64 CG scalars)", "data": "synthetic",
+        "p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
+        "config": {"workload": "real-time radial series: 384x384 grid (192x192 image), 10 coils, 13 spokes/frame "
+                               "rotated k*2pi/65, 7 Newton x 30 CG, previous frame as start and reference",
+                   "n": W.n, "coils": W.ncoils, "spokes": W.spokes, "newton_steps": W.newton_steps,
+                   "cg_iters": W.cg_iters, "frames_timed": K, "graph": "one CUDA graph per frame",
+                   "l2": "flushed before every frame (the frame's ~110 MB working set then stays on chip)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_source": src, "traffic": traffic,
+                     "algo_bytes_per_launch": int(algo[top]), "kernels": kernels},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "finite": finite,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(W)
+    ctx.close()
+    return line
+
+
+# ------------------------------------------------------------------------------------------ CPU oracle ----
+def _oracle_problem(W):
+    import numpy as np
+    import oracle.nlinv_oracle as O
+    from paper_1301_1215_gb300 import synth
+    s = O.Setup(W.n, W.ncoils, W.fov, W.sobolev_a, W.sobolev_l)
+    fr = synth.make_frame(W.n, W.ncoils, W.spokes, seed=W.seed)
+    y0 = O.simulate(s, fr.mask, fr.rho, fr.coils)
+    power = float(np.sum(np.abs(y0) ** 2) / (fr.mask.sum() * W.ncoils))
+    y = y0 + fr.mask * synth.noise_sigma(power, W.snr_db) * fr.noise
+    return O, s, fr, y, synth.initial_guess(W.n, W.ncoils)
+
+
+def cpu_baseline(W):
+    """The oracle, as it stands, on one bounded sample: Newton step 0 of frame 0 (30 CG iterations), scaled to a
+    frame of 7 Newton steps."""
+    O, s, fr, y, x0 = _oracle_problem(W)
+    c0 = cpu_seconds()
+    t0 = time.perf_counter()
+    O.irgnm(s, fr.mask, y, x0, None, 1, W.cg_iters)
+    dt = time.perf_counter() - t0
+    cores = max(1, round((cpu_seconds() - c0) / dt))
+    return {"value": round(1.0 / (dt * W.newton_steps), 6), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "host_cores": os.cpu_count(),
+            "sample": f"Newton step 0 of frame 0 ({W.cg_iters} CG iterations, numpy complex128), "
+                      f"{dt:.2f} s, scaled x{W.newton_steps} to one frame"}
+
+
+def cpu_seconds() -> float:
+    """User + system CPU time of this process (all threads), to report the threads the oracle really used."""
+    import resource
+    ru = resource.getrusage(resource.RUSAGE_SELF)
+    return ru.ru_utime + ru.ru_stime
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import numpy as np
+    W = synth_workload()
+    O, s, fr, y, x0 = _oracle_problem(W)
+    c = O.coils(s, x0)
+    r0, _ = O.residual(s, fr.mask, y, x0)
+    b = O.adjoint(s, fr.mask, x0, r0, c)
+    alpha = W.alpha0
+    r = b.copy()
+    p = r.copy()
+    dx = np.zeros_like(b)
+    rr = O.inner(r, r).real
+
+    def one_iter():
+        nonlocal r, p, dx, rr
+        q = O.normal(s, fr.mask, x0, p, alpha, c)
+        pq = O.inner(p, q).real
+        a = rr / pq if pq > 0 else 0.0
+        dx = dx + a * p
+        r = r - a * q
+        rn = O.inner(r, r).real
+        p = r + (rn / rr if rr else 0.0) * p
+        rr = rn
+
+    for _ in range(args.warmup):
+        one_iter()
+    c0 = cpu_seconds()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_iter()
+    wall = time.perf_counter() - t0
+    cores = max(1, round((cpu_seconds() - c0) / wall))
+    dt = wall / args.steps
+    per_frame = dt * W.newton_steps * (W.cg_iters + 1)
+    value = 1.0 / per_frame
+    return {
+        "metric": METRIC, "value": round(value, 6), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "real-time radial series: 384x384 grid, 10 coils, 13 spokes, 7 Newton x 30 CG",
+                   "sample": "one CG iteration of Newton step 0 per step"},
+        "cpu_baseline": {"value": round(value, 6), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"each step = one CG iteration (normal operator + updates) at 384x384, 10 coils; "
+                                   f"frame = {W.newton_steps} x ({W.cg_iters} + 1) such iterations"},
+        "e2e": {"value": round(value, 6), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def synth_workload():
+    from paper_1301_1215_gb300 import synth
+    return synth.WORKLOADS[WORKLOAD]
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl != "reference":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

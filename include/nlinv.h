@@ -53,7 +53,7 @@ typedef enum {
   NLINV_EINVAL = 1,      /* bad argument (null pointer, unsupported size, host pointer where a device one is due) */
   NLINV_ENOMEM = 2,      /* device memory for the context's workspace could not be allocated */
   NLINV_ECUDA = 3,       /* a CUDA runtime call failed; nlinv_last_error() has its message */
-  NLINV_EBREAKDOWN = 4,  /* CG met Re<p, A p> <= 0 or a non-finite value; the step was skipped (alpha = 0) */
+  NLINV_EBREAKDOWN = 4,  /* CG met a non-finite |r|^2 or Re<p, A p>; the step was skipped (alpha = 0) */
   NLINV_ETIMEOUT = 5     /* nlinv_wait() gave up before the context's queued work finished */
 } nlinv_status;
 
@@ -134,6 +134,14 @@ NLINV_API nlinv_status nlinv_reconstruct(nlinv_ctx* ctx, const nlinv_c32* y, con
  * EBREAKDOWN if a CG breakdown was flagged since the last check (the flag is then cleared), ECUDA on a CUDA
  * error. */
 NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
+
+/* Times the kernels of one CG iteration of Eq. 3 with CUDA events on the context's stream, launching them one by
+ * one reps times on the workspace left by the last nlinv_reconstruct (whose CG state it advances; x is not
+ * changed).  ms_out (HOST, 7 doubles) receives the mean duration in milliseconds of, in order:
+ *   [0] row pass  W^-1, first axis        [1] column pass  W^-1, C (products), FFT   [2] row pass  PSF
+ *   [3] column pass FFT^-1, C^H, FFT       [4] row pass  W^-H + alpha p, Re<p, q>     [5] CG step  [6] CG direction
+ * Waits for the stream.  Errors: EINVAL (reps < 1, NULL pointers, no reconstruction yet), ECUDA. */
+NLINV_API nlinv_status nlinv_profile_cg(nlinv_ctx* ctx, int reps, double* ms_out);
 
 /* Kernel launches queued by the last nlinv_reconstruct, nlinv_forward, ... call (the graph's kernel nodes when a
  * graph was replayed).  -1 for a NULL context. */

@@ -13,7 +13,8 @@ library primitive.  Where the paper leaves a detail open, the reading taken here
 * the Sobolev weight of ``W`` is ``w(k) = (1 + a |k|^2)^(-l/2)`` with ``|k|`` in cycles per grid width,
   ``k_i = g(i)/n`` in ``[-1/2, 1/2)``;
 * Omega is the centred square ``-fov <= g < fov`` (the un-oversampled image of a 2x grid, Sec. 3.2);
-* CG runs a fixed number of iterations from ``dx = 0`` and stops early only when the residual is exactly zero;
+* CG runs a fixed number of iterations from ``dx = 0`` and stops early only at the rounding floor
+  (``|r|^2 = 0`` or ``Re<p, A p> <= 0``, impossible in exact arithmetic for the positive definite system);
 * ``alpha_n = max(alpha_0 q^n, alpha_min)``; a single frame regularises toward its start value.
 """
 from __future__ import annotations
@@ -145,7 +146,8 @@ def cg(apply_A, b: np.ndarray, iters: int) -> np.ndarray:
     """Conjugate gradients for A dx = b, A Hermitian positive definite, from dx = 0, for a fixed count.
 
     Per iteration (Table 1, row CG: two scalar products): q = A p; alpha = |r|^2 / Re<p, q>; dx += alpha p;
-    r -= alpha q; beta = |r_new|^2 / |r|^2; p = r + beta p.  Stops early only if |r|^2 is exactly zero.
+    r -= alpha q; beta = |r_new|^2 / |r|^2; p = r + beta p.  Stops early only when |r|^2 = 0 or Re<p, q> <= 0:
+    for the positive definite system of Eq. 3 both mean that the iteration has reached the rounding floor.
     """
     dx = np.zeros_like(b)
     r = b.copy()
@@ -156,6 +158,8 @@ def cg(apply_A, b: np.ndarray, iters: int) -> np.ndarray:
             break
         q = apply_A(p)
         pq = inner(p, q).real
+        if not pq > 0.0:
+            break
         a = rr / pq
         dx = dx + a * p
         r = r - a * q

@@ -34,7 +34,7 @@ struct Scalars {
   double pq;                     // last Re<p, A p>
   double last;                   // result of a RED_NONE reduction
   double resid[kMaxNewton + 1];  // |y - F x_n| per Newton step
-  int flags;                     // bit 0: CG breakdown (Re<p, A p> <= 0 or not finite)
+  int flags;                     // bit 0: CG breakdown (a non-finite |r|^2 or Re<p, A p>)
   unsigned ticket;               // completion counter of the last-block reduction
 };
 
@@ -121,12 +121,12 @@ __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slo
     case RED_RESID: sc->resid[slot] = sqrt(total); break;
     case RED_RR_INIT: sc->rr = total; break;
     case RED_PQ: {
+      // The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 (or |r|^2 = 0) only occurs once CG has
+      // reached the rounding floor: the step is then empty.  Non-finite values are a breakdown.
       double rr = sc->rr, a = 0.0;
       sc->pq = total;
-      if (rr != 0.0) {
-        if (total > 0.0 && isfinite(total)) a = rr / total;
-        else sc->flags |= 1;
-      }
+      if (!isfinite(total) || !isfinite(rr)) sc->flags |= 1;
+      else if (rr != 0.0 && total > 0.0) a = rr / total;
       sc->alpha = a;
       break;
     }

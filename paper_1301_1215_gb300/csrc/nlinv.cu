@@ -96,6 +96,8 @@ struct nlinv_ctx {
   cudaGraphExec_t graph = nullptr;
   long graph_launches = 0;
   long launches = 0;
+  bool have_state = false;    // a reconstruction has filled the workspace
+  double last_alpha = 0.0;    // alpha_n of the last Newton step
   std::string err;
 };
 
@@ -298,6 +300,7 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     float4* x4 = (float4*)c->x;
     void* args[] = {&d4, &x4, (void*)&n2};
     if ((e = launch(c, (const void*)add_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
+    c->last_alpha = alpha;
     alpha = std::max(alpha * P.alpha_q, P.alpha_min);
   }
   return q_residual(c, P.newton_steps);
@@ -628,6 +631,7 @@ nlinv_status nlinv_reconstruct(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* 
     c->launches = 0;
     NLV_TRY(q_reconstruct(c), "reconstruction");
   }
+  c->have_state = true;
   NLV_TRY(cudaMemcpyAsync(x_inout, c->x, vb, cudaMemcpyDefault, c->stream), "copy x out");
   if (resid || host_x) {
     Scalars hs{};
@@ -638,7 +642,7 @@ nlinv_status nlinv_reconstruct(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* 
     if (hs.flags & 1) {
       int zero = 0;
       cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
-      return fail(c, NLINV_EBREAKDOWN, "CG breakdown: Re<p, A p> <= 0 or not finite");
+      return fail(c, NLINV_EBREAKDOWN, "CG breakdown: a non-finite |r|^2 or Re<p, A p>");
     }
   }
   return NLINV_OK;
@@ -668,8 +672,63 @@ nlinv_status nlinv_wait(nlinv_ctx* c, double timeout_s) {
   if (flags & 1) {
     int zero = 0;
     NLV_TRY(cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
-    return fail(c, NLINV_EBREAKDOWN, "CG breakdown: Re<p, A p> <= 0 or not finite");
+    return fail(c, NLINV_EBREAKDOWN, "CG breakdown: a non-finite |r|^2 or Re<p, A p>");
   }
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
+  if (!c) return NLINV_EINVAL;
+  if (reps < 1 || !ms_out) return fail(c, NLINV_EINVAL, "reps must be >= 1 and ms_out non-NULL");
+  if (!c->have_state) return fail(c, NLINV_EINVAL, "run nlinv_reconstruct before nlinv_profile_cg");
+  constexpr int K = 7;
+  cudaEvent_t ev[K + 1];
+  for (int i = 0; i <= K; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
+  double acc[K] = {0};
+  const float al = (float)c->last_alpha;
+  const long n2 = c->vec / 2;
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < reps && e == cudaSuccess; ++it) {
+    int k = 0;
+    auto mark = [&]() { if (e == cudaSuccess) e = cudaEventRecord(ev[k++], c->stream); };
+    mark();
+    KArgs a = base_args(c);
+    a.src = c->p + c->plane; a.dst = c->T;
+    if (e == cudaSuccess) e = row(c, nlv::ROW_W_IFFT, a);
+    mark();
+    a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.coil = c->coil;
+    if (e == cudaSuccess) e = col(c, nlv::COL_IFFT_PROD_FFT, a);
+    mark();
+    a = base_args(c); a.src = c->T; a.dst = c->T; a.mask = c->mask;
+    if (e == cudaSuccess) e = row(c, nlv::ROW_PSF, a);
+    mark();
+    if (e == cudaSuccess) e = q_adj_col(c, c->x);
+    mark();
+    a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.zsum = c->zsum; a.alpha = al;
+    a.reduce = nlv::RED_PQ;
+    if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
+    mark();
+    a = base_args(c); a.reduce = nlv::RED_RR_UPDATE;
+    const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
+    float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
+    void* args1[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
+    if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args1);
+    mark();
+    const float4* rr4 = (const float4*)c->r;
+    float4* pp4 = (float4*)c->p;
+    void* args2[] = {&a, &rr4, &pp4, (void*)&n2};
+    if (e == cudaSuccess) e = launch(c, (const void*)cg_dir_kernel, c->vec_blocks, kVecThreads, 0, args2);
+    mark();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
+    }
+  }
+  for (int i = 0; i <= K; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "nlinv_profile_cg");
+  for (int i = 0; i < K; ++i) ms_out[i] = acc[i] / reps;
   return NLINV_OK;
 }
 
