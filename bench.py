@@ -153,13 +153,12 @@ def cg_bytes(n: int, J: int, fov: int):
     q = h * h                         # fraction kept as Omega
     mask = n * n
     return {
-        "row W^-1": J * U * (1 + h),
-        "col W^-1/C/FFT": J * U * (h + q + h) + 2 * q * U,
+        "row p-update/W^-1": J * U * (3 + h),                          # r_c, p_c in; p_c, T out
+        "col W^-1/C/FFT": J * U * (h + q + h) + 3 * q * U,             # T, c in; T out; rho, r_rho, p_rho on Omega
         "row PSF": J * U * 2 * h + mask,
-        "col FFT^-1/C^H/FFT": J * U * (h + q + h + q) + q * U,
-        "row W^-H+alpha p": J * U * (h + q) + 2 * (1 + J) * U,
+        "col FFT^-1/C^H/FFT": J * U * (h + q + h + q) + q * U,         # T, c in; T, channel products out; rho
+        "row W^-H+alpha p": J * U * (h + q) + 2 * J * U + 4 * U,       # T, products, p in; q out; rho: r, p in, p, q out
         "cg step": 6 * (1 + J) * U,
-        "cg direction": 3 * (1 + J) * U,
     }
 
 

@@ -42,10 +42,9 @@ struct KArgs {
   int N, J, f, Wc;          // grid side, coils, half-width of Omega, compact width 2f
   int nrows;                // row passes: rows of the coil planes (J*N); column passes: J
   int coil_blocks;          // row passes with a rho part: blocks that work on coil rows
-  float sob_a;              // Sobolev weight (1 + a |k|^2)^(-l/2)
-  float sob_halfl;          // l/2
-  int sob_ipow;             // l/2 as an integer when it is one in [0, 64], else -1
+  const float* wtab;        // Sobolev weight w(k) = (1 + a |k|^2)^(-l/2), N x N natural order
   float alpha;              // alpha_n of Eq. 3 for the normal operator and the right-hand side
+  int pupd;                 // CG passes: first form p = r + beta p (beta from Scalars) and write it back
   const float2* src;        // main input planes
   float2* dst;              // main output planes
   const float2* rho;        // rho of the linearisation point (natural N x N)
@@ -69,30 +68,28 @@ struct KArgs {
   int slot;                 // RED_RESID index
 };
 
+// ------------------------------------------------------------------------------- dependent launches ----
+// Every kernel is launched with programmatic stream serialisation: it may be scheduled while the kernel before it
+// in the stream is still running.  griddepcontrol.wait blocks until that kernel has completed and its memory is
+// visible, so it must come before the first global memory access; launch_dependents then lets the next kernel be
+// scheduled as soon as every block of this one has started.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------------------------------- geometry ----
 __device__ __forceinline__ bool in_omega(int e, int N, int f) { return e < f || e >= N - f; }
 __device__ __forceinline__ int to_compact(int e, int N, int f) { return e < f ? e : e - (N - 2 * f); }
 __device__ __forceinline__ int to_natural(int cc, int N, int f) { return cc < f ? cc : cc + (N - 2 * f); }
 
-// Sobolev weight of W (Sec. 3.1) at natural index (k1, k2): (1 + a (g1^2 + g2^2)/N^2)^(-l/2), g signed.
+// Sobolev weight of W (Sec. 3.1) at natural index (k1, k2), from the table built on the host in double precision.
 __device__ __forceinline__ float sobolev_w(int k1, int k2, const KArgs& A) {
-  const int N = A.N;
-  int g1 = k1 < N / 2 ? k1 : k1 - N;
-  int g2 = k2 < N / 2 ? k2 : k2 - N;
-  float k2n = (float)(g1 * g1 + g2 * g2) / (float)(N * N);
-  float d = fmaf(A.sob_a, k2n, 1.0f);
-  if (A.sob_ipow >= 0) {
-    float t = __frcp_rn(d), w = 1.0f;
-    int e = A.sob_ipow;
-    while (e) {
-      if (e & 1) w *= t;
-      t *= t;
-      e >>= 1;
-    }
-    return w;
-  }
-  return powf(d, -A.sob_halfl);
+  return __ldg(&A.wtab[(size_t)k1 * A.N + k2]);
 }
+
+// beta of the pending direction update p = r + beta p (CG, Table 1)
+__device__ __forceinline__ float cg_beta(const KArgs& A) { return (float)A.sc->beta; }
 
 // ----------------------------------------------------------------------------------------- reductions ----
 __device__ __forceinline__ double warp_sum(double v) {
@@ -119,7 +116,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slot, double total) {
   switch (reduce) {
     case RED_RESID: sc->resid[slot] = sqrt(total); break;
-    case RED_RR_INIT: sc->rr = total; break;
+    case RED_RR_INIT: sc->rr = total; sc->beta = 0.0; break;
     case RED_PQ: {
       // The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 (or |r|^2 = 0) only occurs once CG has
       // reached the rounding floor: the step is then empty.  Non-finite values are a breakdown.
@@ -191,25 +188,46 @@ template <int N1, int N2> struct RowCfg {
   static constexpr size_t SMEM = (size_t)LANES * S::SM_LANE * sizeof(float2);
 };
 
-// rho plane of the adjoint / normal / right-hand-side outputs: sum of the channel products on Omega (the
-// channel summation of Table 1) plus the mode's alpha term.
+// rho plane of the adjoint / normal / right-hand-side outputs: the sum of the channel products over the coils on
+// Omega (the channel summation of Table 1) plus the mode's alpha term.  Each thread takes kRhoEPT consecutive
+// pixels of one row; the coil loads are independent so that many are in flight at once.
+constexpr int kRhoEPT = 8;
+
 template <int MODE>
-__device__ __forceinline__ float rho_row(const KArgs& A, int e1, int idx, int TL) {
-  const int N = A.N, f = A.f, Wc = A.Wc;
+__device__ __forceinline__ float rho_part(const KArgs& A, int rb) {
+  const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
+  const long first = ((long)rb * blockDim.x + threadIdx.x) * kRhoEPT;
+  float acc = 0.f;
+  if (first >= (long)N * N) return acc;
+  const int e1 = (int)(first / N), e20 = (int)(first % N);
   const bool row_in = in_omega(e1, N, f);
   const int cr = to_compact(e1, N, f);
-  float acc = 0.f;
-  for (int e2 = idx; e2 < N; e2 += TL) {
+  const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
+#pragma unroll
+  for (int t = 0; t < kRhoEPT; ++t) {
+    const int e2 = e20 + t;
+    const size_t o = (size_t)e1 * N + e2;
     float2 z = make_float2(0.f, 0.f);
     if (row_in && in_omega(e2, N, f)) {
-      const int cc = to_compact(e2, N, f);
-      for (int j = 0; j < A.J; ++j) z = cadd(z, A.zsum[((size_t)j * Wc + cr) * Wc + cc]);
+      const float2* zp = A.zsum + (size_t)cr * Wc + to_compact(e2, N, f);
+      const size_t stride = (size_t)Wc * Wc;
+      int j = 0;
+      for (; j + 4 <= J; j += 4) {
+        float2 a0 = zp[(j + 0) * stride], a1 = zp[(j + 1) * stride];
+        float2 a2 = zp[(j + 2) * stride], a3 = zp[(j + 3) * stride];
+        z = cadd(z, cadd(cadd(a0, a1), cadd(a2, a3)));
+      }
+      for (; j < J; ++j) z = cadd(z, zp[j * stride]);
     }
-    const size_t o = (size_t)e1 * N + e2;
     if constexpr (MODE == ROW_FFT_W_ADJ) {
       A.dst[o] = z;
     } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
       float2 pv = A.p[o];
+      if (A.pupd) {
+        const float2 rv = A.r[o];
+        pv = make_float2(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y));
+        const_cast<float2*>(A.p)[o] = pv;
+      }
       float2 q = make_float2(fmaf(A.alpha, pv.x, z.x), fmaf(A.alpha, pv.y, z.y));
       A.dst[o] = q;
       acc += pv.x * q.x + pv.y * q.y;
@@ -231,14 +249,14 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
   using T = RowTraits<MODE>;
   constexpr int N = S::N, TL = S::TL, E = S::E;
   extern __shared__ float2 smem[];
+  pdl_enter();
   const int lane = threadIdx.x / TL, idx = threadIdx.x % TL;
   const int f = A.f, Wc = A.Wc;
   float acc = 0.f;
 
   if constexpr (T::has_rho) {
     if ((int)blockIdx.x >= A.coil_blocks) {
-      const int e1 = ((int)blockIdx.x - A.coil_blocks) * RowCfg<N1, N2>::LANES + lane;
-      if (e1 < N) acc = rho_row<MODE>(A, e1, idx, TL);
+      acc = rho_part<MODE>(A, (int)blockIdx.x - A.coil_blocks);
       if constexpr (T::reduces) grid_reduce(acc, A);
       return;
     }
@@ -249,6 +267,7 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
   const int e1 = R % N;
   float2* sm = smem + lane * S::SM_LANE;
   const float rs = rsqrtf((float)N);
+  const float beta = (MODE == ROW_W_IFFT && A.pupd) ? cg_beta(A) : 0.f;
   float2 v[E];
 
   // ---- load, layout A: thread a < N1 holds row elements a + N1*m
@@ -261,7 +280,14 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
         if constexpr (T::load_compact) {
           if (in_omega(e2, N, f)) val = A.src[(size_t)R * Wc + to_compact(e2, N, f)];
         } else if constexpr (MODE == ROW_W_IFFT) {
-          val = cscale(A.src[(size_t)R * N + e2], sobolev_w(e1, e2, A) * rs);
+          const size_t o = (size_t)R * N + e2;
+          float2 sv = A.src[o];
+          if (A.pupd) {            // p = r + beta p on the coil planes, written back for the later passes
+            const float2 rv = A.r[o];
+            sv = make_float2(fmaf(beta, sv.x, rv.x), fmaf(beta, sv.y, rv.y));
+            const_cast<float2*>(A.src)[o] = sv;
+          }
+          val = cscale(sv, sobolev_w(e1, e2, A) * rs);
         } else {  // ROW_P_IFFT
           val = A.mask[(size_t)e1 * N + e2] ? cscale(A.src[(size_t)R * N + e2], rs) : make_float2(0.f, 0.f);
         }
@@ -362,6 +388,7 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
   extern __shared__ float2 smem[];
+  pdl_enter();
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
   const int f = A.f, Wc = A.Wc;
   const int strips = (Wc + C - 1) / C;
@@ -373,6 +400,7 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
   const float rs = rsqrtf((float)N);
   const size_t tbase = (size_t)j * N * Wc + cc;       // T element (row e1) at tbase + e1*Wc
   const size_t cbase = (size_t)j * Wc * Wc + cc;      // compact coil element (row cr) at cbase + cr*Wc
+  const float beta = (MODE == COL_IFFT_PROD_FFT && A.pupd) ? cg_beta(A) : 0.f;
   float2 v[E];
 
   if constexpr (MODE == COL_PROD_FFT || MODE == COL_SIM_FFT) {
@@ -428,7 +456,12 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
             const float2 c = A.coil[cbase + (size_t)to_compact(e1, N, f) * Wc];
             const float2 rh = A.rho[on];
             if constexpr (MODE == COL_IFFT_PROD_FFT) {
-              out = cadd(cmul(A.drho[on], c), cmul(rh, u));
+              float2 dr = A.drho[on];
+              if (A.pupd) {          // rho part of p = r + beta p (written later by the last row pass)
+                const float2 rv = A.r[on];
+                dr = make_float2(fmaf(beta, dr.x, rv.x), fmaf(beta, dr.y, rv.y));
+              }
+              out = cadd(cmul(dr, c), cmul(rh, u));
             } else {  // COL_IFFT_ADJ_FFT
               A.zsum[cbase + (size_t)to_compact(e1, N, f) * Wc] = cmulc(c, u);
               out = cmulc(rh, u);

@@ -13,6 +13,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -34,6 +35,7 @@ thread_local std::string g_create_error;
 // dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.   n2 = number of complex pairs (float4 accesses).
 __global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, const float4* __restrict__ q4,
                                float4* __restrict__ r4, float4* __restrict__ dx4, long n2) {
+  nlv::pdl_enter();
   const float a = (float)A.sc->alpha;
   float acc = 0.f;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
@@ -47,18 +49,9 @@ __global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, con
   nlv::grid_reduce(acc, A);
 }
 
-// p = r + beta p
-__global__ void cg_dir_kernel(const KArgs A, const float4* __restrict__ r4, float4* __restrict__ p4, long n2) {
-  const float b = (float)A.sc->beta;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
-    float4 r = r4[i], p = p4[i];
-    p.x = fmaf(b, p.x, r.x); p.y = fmaf(b, p.y, r.y); p.z = fmaf(b, p.z, r.z); p.w = fmaf(b, p.w, r.w);
-    p4[i] = p;
-  }
-}
-
 // x += dx
 __global__ void add_kernel(const float4* __restrict__ d4, float4* __restrict__ x4, long n2) {
+  nlv::pdl_enter();
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
     float4 d = d4[i], x = x4[i];
     x.x += d.x; x.y += d.y; x.z += d.z; x.w += d.w;
@@ -67,6 +60,7 @@ __global__ void add_kernel(const float4* __restrict__ d4, float4* __restrict__ x
 }
 
 constexpr int kVecThreads = 256;
+constexpr int kProfileKernels = 6;   // kernels of one CG iteration, in the order nlinv_profile_cg reports them
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -89,6 +83,7 @@ struct nlinv_ctx {
   float2 *r = nullptr, *p = nullptr, *q = nullptr, *dx = nullptr;
   float2 *T = nullptr, *coil = nullptr, *zsum = nullptr;
   float2 *twA = nullptr, *twB = nullptr;
+  float* wtab = nullptr;      // Sobolev weight, N x N
   uint8_t* mask = nullptr;
   double* partials = nullptr;
   Scalars* sc = nullptr;
@@ -97,6 +92,7 @@ struct nlinv_ctx {
   long graph_launches = 0;
   long launches = 0;
   bool have_state = false;    // a reconstruction has filled the workspace
+  bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   std::string err;
 };
@@ -124,10 +120,7 @@ KArgs base_args(const nlinv_ctx* c) {
   a.J = c->J;
   a.f = c->f;
   a.Wc = c->Wc;
-  a.sob_a = (float)c->prm.sobolev_a;
-  a.sob_halfl = (float)(0.5 * c->prm.sobolev_l);
-  const double hl = 0.5 * c->prm.sobolev_l;
-  a.sob_ipow = (hl == std::floor(hl) && hl >= 0 && hl <= 64) ? (int)hl : -1;
+  a.wtab = c->wtab;
   a.twA = c->twA;
   a.twB = c->twB;
   a.partials = c->partials;
@@ -139,7 +132,10 @@ KArgs base_args(const nlinv_ctx* c) {
 int row_blocks(const nlinv_ctx* c, bool with_rho) {
   const int L = c->k->row_lanes;
   int b = (c->J * c->N + L - 1) / L;
-  if (with_rho) b += (c->N + L - 1) / L;
+  if (with_rho) {
+    const long per = (long)c->k->row_threads * nlv::kRhoEPT;
+    b += (int)((c->plane + per - 1) / per);
+  }
   return b;
 }
 
@@ -148,9 +144,20 @@ int col_blocks(const nlinv_ctx* c) {
   return c->J * ((c->Wc + C - 1) / C);
 }
 
+// Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh) unless it is switched off.
 cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
   c->launches++;
-  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, c->stream);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = c->pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
@@ -216,11 +223,30 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
-// One CG iteration on (DF^H DF + alpha) for linearisation point x: q, alpha, dx, r, beta, p.
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool update_dir) {
-  cudaError_t e = q_dir(c, x, c->p);
-  if (e != cudaSuccess) return e;
+// One CG iteration on (DF^H DF + alpha) for linearisation point x.  The direction update p = r + beta p of the
+// previous iteration is folded into the passes that first read p (beta = 0 right after the right-hand side).
+//   K1 row  p_c = r_c + beta p_c; T = W^-1 p_c (first axis)
+//   K2 col  drho = r_rho + beta p_rho; T = FFT_col(M (drho c_j + rho W^-1 p_c))
+//   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> -> alpha
+//   K6      dx += alpha p, r -= alpha q, |r|^2 -> beta
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   KArgs a = base_args(c);
+  a.src = c->p + c->plane;
+  a.r = c->r + c->plane;
+  a.pupd = 1;
+  a.dst = c->T;
+  cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
+  if (e != cudaSuccess) return e;
+  a = base_args(c);
+  a.src = c->T;
+  a.dst = c->T;
+  a.rho = x;
+  a.drho = c->p;
+  a.r = c->r;
+  a.pupd = 1;
+  a.coil = c->coil;
+  if ((e = col(c, nlv::COL_IFFT_PROD_FFT, a)) != cudaSuccess) return e;
+  a = base_args(c);
   a.src = c->T;
   a.dst = c->T;
   a.mask = c->mask;
@@ -230,6 +256,8 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool update_di
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
+  a.r = c->r;
+  a.pupd = 1;
   a.zsum = c->zsum;
   a.alpha = alpha;
   a.reduce = nlv::RED_PQ;
@@ -239,17 +267,8 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool update_di
   const long n2 = c->vec / 2;
   const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
   float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
-  {
-    void* args[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
-    if ((e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
-  }
-  if (update_dir) {
-    const float4* rr4 = (const float4*)c->r;
-    float4* pp4 = (float4*)c->p;
-    void* args[] = {&a, &rr4, &pp4, (void*)&n2};
-    if ((e = launch(c, (const void*)cg_dir_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  void* args[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
+  return launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args);
 }
 
 // Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
@@ -294,7 +313,7 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     a.reduce = nlv::RED_RR_INIT;
     if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
     for (int i = 0; i < P.cg_iters; ++i)
-      if ((e = q_cg_iter(c, c->x, al, i + 1 < P.cg_iters)) != cudaSuccess) return e;
+      if ((e = q_cg_iter(c, c->x, al)) != cudaSuccess) return e;
     const long n2 = c->vec / 2;
     const float4* d4 = (const float4*)c->dx;
     float4* x4 = (float4*)c->x;
@@ -392,6 +411,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "0") != 0;
   c->vec_blocks = std::max(1, sms) * 4;
 
   // dynamic shared memory above the 48 KB default
@@ -408,11 +428,12 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   const size_t Tb = align_up((size_t)c->J * c->N * c->Wc * cplx, 256);
   const size_t cb = align_up((size_t)c->J * c->Wc * c->Wc * cplx, 256);
   const size_t twb = align_up((size_t)c->N * cplx, 256);
+  const size_t wb = align_up((size_t)c->plane * sizeof(float), 256);
   const size_t maskb = align_up((size_t)c->plane, 256);
   const int max_blocks = std::max(row_blocks(c, true), c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
-  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + maskb + partb + scb;
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + partb + scb;
   e = cudaMalloc(&c->base, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -436,6 +457,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   c->zsum = (float2*)take(cb);
   c->twA = (float2*)take(twb);
   c->twB = (float2*)take(twb);
+  c->wtab = (float*)take(wb);
   c->mask = (uint8_t*)take(maskb);
   c->partials = (double*)take(partb);
   c->sc = (Scalars*)take(scb);
@@ -452,9 +474,18 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
     for (int a = 0; a < N1; ++a) ta[k2 * N1 + a] = tw((long)a * k2);
   for (int k2 = 0; k2 < N1; ++k2)
     for (int a = 0; a < N2; ++a) tb[k2 * N2 + a] = tw((long)a * k2);
+  // Sobolev weight w(k) = (1 + a |k|^2)^(-l/2), |k|^2 = (g1^2 + g2^2) / N^2 with signed natural-order indices
+  std::vector<float> wt((size_t)c->plane);
+  for (int k1 = 0; k1 < N; ++k1)
+    for (int k2 = 0; k2 < N; ++k2) {
+      const double g1 = k1 < N / 2 ? k1 : k1 - N, g2 = k2 < N / 2 ? k2 : k2 - N;
+      const double kk = (g1 * g1 + g2 * g2) / ((double)N * N);
+      wt[(size_t)k1 * N + k2] = (float)std::pow(1.0 + params->sobolev_a * kk, -0.5 * params->sobolev_l);
+    }
   e = cudaMemset(c->base, 0, total);
   if (e == cudaSuccess) e = cudaMemcpy(c->twA, ta.data(), N * cplx, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->twB, tb.data(), N * cplx, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->wtab, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     g_create_error = std::string("context set-up: ") + cudaGetErrorString(e);
@@ -681,7 +712,7 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   if (!c) return NLINV_EINVAL;
   if (reps < 1 || !ms_out) return fail(c, NLINV_EINVAL, "reps must be >= 1 and ms_out non-NULL");
   if (!c->have_state) return fail(c, NLINV_EINVAL, "run nlinv_reconstruct before nlinv_profile_cg");
-  constexpr int K = 7;
+  constexpr int K = kProfileKernels;
   cudaEvent_t ev[K + 1];
   for (int i = 0; i <= K; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
   double acc[K] = {0};
@@ -693,10 +724,11 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     auto mark = [&]() { if (e == cudaSuccess) e = cudaEventRecord(ev[k++], c->stream); };
     mark();
     KArgs a = base_args(c);
-    a.src = c->p + c->plane; a.dst = c->T;
+    a.src = c->p + c->plane; a.r = c->r + c->plane; a.pupd = 1; a.dst = c->T;
     if (e == cudaSuccess) e = row(c, nlv::ROW_W_IFFT, a);
     mark();
-    a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.coil = c->coil;
+    a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.r = c->r; a.pupd = 1;
+    a.coil = c->coil;
     if (e == cudaSuccess) e = col(c, nlv::COL_IFFT_PROD_FFT, a);
     mark();
     a = base_args(c); a.src = c->T; a.dst = c->T; a.mask = c->mask;
@@ -704,8 +736,8 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     mark();
     if (e == cudaSuccess) e = q_adj_col(c, c->x);
     mark();
-    a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.zsum = c->zsum; a.alpha = al;
-    a.reduce = nlv::RED_PQ;
+    a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum;
+    a.alpha = al; a.reduce = nlv::RED_PQ;
     if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
     mark();
     a = base_args(c); a.reduce = nlv::RED_RR_UPDATE;
@@ -713,11 +745,6 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
     void* args1[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
     if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args1);
-    mark();
-    const float4* rr4 = (const float4*)c->r;
-    float4* pp4 = (float4*)c->p;
-    void* args2[] = {&a, &rr4, &pp4, (void*)&n2};
-    if (e == cudaSuccess) e = launch(c, (const void*)cg_dir_kernel, c->vec_blocks, kVecThreads, 0, args2);
     mark();
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {

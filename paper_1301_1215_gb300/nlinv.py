@@ -196,13 +196,13 @@ class Nlinv:
         """Waits for the context's queued work (raises NlinvError with ETIMEOUT or EBREAKDOWN)."""
         self._check(self._lib.nlinv_wait(self._h, float(timeout_s)))
 
-    CG_KERNELS = ("row W^-1", "col W^-1/C/FFT", "row PSF", "col FFT^-1/C^H/FFT", "row W^-H+alpha p", "cg step",
-                  "cg direction")
+    CG_KERNELS = ("row p-update/W^-1", "col W^-1/C/FFT", "row PSF", "col FFT^-1/C^H/FFT", "row W^-H+alpha p",
+                  "cg step")
 
     def profile_cg(self, reps: int = 20) -> dict:
         """Mean CUDA-event duration (ms) of each kernel of one CG iteration, launched one by one on the state of
         the last reconstruction (advances its CG state)."""
-        ms = (C.c_double * 7)()
+        ms = (C.c_double * len(self.CG_KERNELS))()
         self._begin()
         self._check(self._lib.nlinv_profile_cg(self._h, int(reps), ms))
         self._end()
