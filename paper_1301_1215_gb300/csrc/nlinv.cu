@@ -92,7 +92,7 @@ struct nlinv_ctx {
   long graph_launches = 0;
   long launches = 0;
   bool have_state = false;    // a reconstruction has filled the workspace
-  bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
+  bool pdl = false;           // programmatic dependent launches (NLINV_PDL=1 turns them on; slower here)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   std::string err;
 };
@@ -144,7 +144,8 @@ int col_blocks(const nlinv_ctx* c) {
   return c->J * ((c->Wc + C - 1) / C);
 }
 
-// Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh) unless it is switched off.
+// Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh) when it is switched on; measured
+// on the 384 x 384, 10-coil series it slowed each frame down (16.1 -> 18.6 ms), so it is off by default.
 cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
   c->launches++;
   cudaLaunchConfig_t cfg{};
@@ -411,7 +412,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "0") != 0;
+  if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "1") == 0;
   c->vec_blocks = std::max(1, sms) * 4;
 
   // dynamic shared memory above the 48 KB default
