@@ -148,6 +148,25 @@ NLINV_API nlinv_status nlinv_profile_cg(nlinv_ctx* ctx, int reps, double* ms_out
  * graph was replayed).  -1 for a NULL context. */
 NLINV_API long nlinv_last_launch_count(const nlinv_ctx* ctx);
 
+/* F x like nlinv_forward, but without a context and without allocating any device memory.  The paper has no
+ * counterpart; it serves callers that may not allocate device memory when they apply F: a real-time loop that
+ * reserves its GPU memory up front and must not see a cudaMalloc fail or stall mid-series, or a host framework
+ * that owns every device allocation.  Such callers cannot use nlinv_create, whose workspace is allocated.
+ * The scratch (the Omega-column transform buffer, the coil maps, the twiddle and Sobolev tables) lives in one
+ * file-scope device array of 16 MiB that every GPU loading this library holds until the process exits; a call
+ * whose n, ncoils and fov need more than that is rejected with EINVAL (384 x 384 with 10 coils and fov = n/4 fits;
+ * 512 x 512 with 16 coils does not).  The caller passes x (1+J planes), mask and y_out (J planes), all device
+ * pointers, and a cudaStream_t (NULL = legacy default stream); params supplies n, ncoils, fov, sobolev_a and
+ * sobolev_l (the other fields are ignored).
+ * The first call on a device finds the array's device address, and the first call, and every call whose n or
+ * Sobolev parameters differ from the previous call's on that device, writes the tables and waits for the stream.
+ * All calls on a device share the one array and every call overwrites it (nothing in it has to start at zero):
+ * calls that overlap on the GPU -- on different streams or host threads -- race and give wrong results.
+ * Errors: EINVAL (bad params, NULL or host pointers, sizes beyond the scratch), ECUDA; message via
+ * nlinv_last_error(NULL). */
+NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* params, void* stream, const nlinv_c32* x,
+                                             const uint8_t* mask, nlinv_c32* y_out);
+
 /* Message of the last failed call on ctx (or of the last failed nlinv_create when ctx is NULL).  The string is
  * owned by the library and stays valid until the next call on the same context. */
 NLINV_API const char* nlinv_last_error(const nlinv_ctx* ctx);

@@ -38,6 +38,7 @@ SIGNATURES = {
     "nlinv_reconstruct": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "nlinv_wait": (_int, [_vp, _dbl]),
     "nlinv_profile_cg": (_int, [_vp, _int, C.POINTER(_dbl)]),
+    "nlinv_forward_noalloc": (_int, [C.POINTER(Params), _vp, _vp, _vp, _vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
     "nlinv_last_error": (C.c_char_p, [_vp]),
 }

@@ -99,6 +99,13 @@ struct nlinv_ctx {
 
 namespace {
 
+}  // namespace
+
+// Records the message returned by nlinv_last_error(NULL) (used by the calls that take no context).
+void nlv_set_global_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
+
 nlinv_status fail(nlinv_ctx* c, nlinv_status s, const std::string& msg) {
   if (c) c->err = msg; else g_create_error = msg;
   return s;
