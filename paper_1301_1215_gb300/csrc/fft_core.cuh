@@ -197,16 +197,17 @@ template <int A, int B> struct Split {
 // Layout A(P1, P2) -> layout B(P1, P2) for one lane of P1*P2 points.
 //   v      register slots of this thread (v[0..P2) valid on entry if idx < P1; v[0..P1) valid on exit if idx < P2)
 //   sm     this lane's shared-memory exchange area (>= P2*(P1+1) float2)
-//   tw     table tw[k2*P1 + a] = exp(-2 pi i a k2 / (P1 P2)) (forward sign; conjugated for D = +1)
+//   tw     table tw[k2*P1 + a] = exp(-2 pi i a k2 / (P1 P2)) (forward sign; conjugated for D = +1), in shared
+//          memory
 // Contains two __syncthreads(): every thread of the CTA must call it.
 template <int P1, int P2, int D, int E>
-__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* __restrict__ tw, int idx) {
+__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx) {
   constexpr int S = P1 + 1;
   if (idx < P1) {
     RegDFT<P2, D>::run(v);
     static_for<P2>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
-      float2 w = __ldg(&tw[k2 * P1 + idx]);
+      float2 w = tw[k2 * P1 + idx];
       if (D > 0) w.y = -w.y;
       sm[k2 * S + idx] = (k2 == 0) ? v[k2] : cmul(v[k2], w);
     });

@@ -161,6 +161,31 @@ __device__ __forceinline__ void grid_reduce(float mine, const KArgs& A) {
   }
 }
 
+// ------------------------------------------------------------------------------------ async staging ----
+// Side inputs of a pass (sampling pattern, weights, CG vectors, coil maps, rho) and the twiddle tables are copied
+// into shared memory with cp.async at the start of every pass, together with the main loads, so that all load
+// latencies overlap once instead of stalling the pointwise steps between the transforms.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Copies nbytes (a multiple of 16, both addresses 16-byte aligned) with all threads of the block.
+__device__ __forceinline__ void stage_bytes(void* sdst, const void* gsrc, int nbytes) {
+  for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x)
+    cp_async16((char*)sdst + 16 * i, (const char*)gsrc + 16 * i);
+}
+
+__host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+
 // ------------------------------------------------------------------------------------------ row passes ----
 enum RowMode : int {
   ROW_W_IFFT = 0,        // T <- compact cols of FFT^-1_row(w * src / sqrt N)            (W^-1, first axis)
@@ -179,18 +204,48 @@ template <int MODE> struct RowTraits {
   static constexpr bool inverse_first = (MODE == ROW_W_IFFT || MODE == ROW_P_IFFT);
   static constexpr bool has_rho = (MODE == ROW_FFT_W_ADJ || MODE == ROW_FFT_W_NORMAL || MODE == ROW_FFT_W_RHS);
   static constexpr bool reduces = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL || MODE == ROW_FFT_W_RHS);
+  // side inputs staged per row: sampling-pattern row (bytes), weight row (floats), complex rows
+  static constexpr bool s_mask = (MODE == ROW_PSF || MODE == ROW_FFT_P_OUT || MODE == ROW_FFT_RESID);
+  static constexpr bool s_w = has_rho;
+  static constexpr int s_cplx = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL) ? 1
+                              : (MODE == ROW_FFT_W_RHS) ? 2 : 0;
 };
+
+// Shared-memory layout of a row pass (byte offsets), identical on host and device.
+struct RowSmem {
+  size_t xch, tw, mask, w, cplx, total;
+};
+__host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_lane) {
+  RowSmem L{};
+  const bool m = (mode == ROW_PSF || mode == ROW_FFT_P_OUT || mode == ROW_FFT_RESID);
+  const bool w = (mode == ROW_FFT_W_ADJ || mode == ROW_FFT_W_NORMAL || mode == ROW_FFT_W_RHS);
+  const int nc = (mode == ROW_FFT_RESID || mode == ROW_FFT_W_NORMAL) ? 1 : (mode == ROW_FFT_W_RHS) ? 2 : 0;
+  L.xch = 0;
+  L.tw = align16((size_t)lanes * sm_lane * 8);
+  L.mask = L.tw + align16((size_t)2 * N * 8);
+  L.w = L.mask + (m ? align16((size_t)lanes * N) : 0);
+  L.cplx = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
+  L.total = L.cplx + (size_t)nc * lanes * N * 8;
+  return L;
+}
+
+#ifndef NLV_ROW_THREADS
+#define NLV_ROW_THREADS 256
+#endif
+#ifndef NLV_COL_C
+#define NLV_COL_C 8
+#endif
 
 template <int N1, int N2> struct RowCfg {
   using S = Split<N1, N2>;
-  static constexpr int LANES = (256 / S::TL) >= 16 ? 16 : (256 / S::TL) >= 8 ? 8 : (256 / S::TL) >= 4 ? 4 : 2;
+  static constexpr int LANES = (NLV_ROW_THREADS / S::TL) >= 16 ? 16 : (NLV_ROW_THREADS / S::TL) >= 8 ? 8
+                             : (NLV_ROW_THREADS / S::TL) >= 4 ? 4 : (NLV_ROW_THREADS / S::TL) >= 2 ? 2 : 1;
   static constexpr int THREADS = LANES * S::TL;
-  static constexpr size_t SMEM = (size_t)LANES * S::SM_LANE * sizeof(float2);
 };
 
 // rho plane of the adjoint / normal / right-hand-side outputs: the sum of the channel products over the coils on
 // Omega (the channel summation of Table 1) plus the mode's alpha term.  Each thread takes kRhoEPT consecutive
-// pixels of one row; the coil loads are independent so that many are in flight at once.
+// pixels of one row; all loads are issued before the first store.
 constexpr int kRhoEPT = 8;
 
 template <int MODE>
@@ -202,42 +257,46 @@ __device__ __forceinline__ float rho_part(const KArgs& A, int rb) {
   const int e1 = (int)(first / N), e20 = (int)(first % N);
   const bool row_in = in_omega(e1, N, f);
   const int cr = to_compact(e1, N, f);
-  const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
+  const size_t o0 = (size_t)e1 * N + e20;
+  float2 z[kRhoEPT], a[kRhoEPT], b[kRhoEPT];
 #pragma unroll
   for (int t = 0; t < kRhoEPT; ++t) {
     const int e2 = e20 + t;
-    const size_t o = (size_t)e1 * N + e2;
-    float2 z = make_float2(0.f, 0.f);
+    z[t] = make_float2(0.f, 0.f);
     if (row_in && in_omega(e2, N, f)) {
       const float2* zp = A.zsum + (size_t)cr * Wc + to_compact(e2, N, f);
       const size_t stride = (size_t)Wc * Wc;
-      int j = 0;
-      for (; j + 4 <= J; j += 4) {
-        float2 a0 = zp[(j + 0) * stride], a1 = zp[(j + 1) * stride];
-        float2 a2 = zp[(j + 2) * stride], a3 = zp[(j + 3) * stride];
-        z = cadd(z, cadd(cadd(a0, a1), cadd(a2, a3)));
-      }
-      for (; j < J; ++j) z = cadd(z, zp[j * stride]);
+      for (int j = 0; j < J; ++j) z[t] = cadd(z[t], zp[j * stride]);
     }
+    if constexpr (MODE == ROW_FFT_W_NORMAL) {
+      a[t] = A.p[o0 + t];
+      b[t] = A.pupd ? A.r[o0 + t] : make_float2(0.f, 0.f);
+    } else if constexpr (MODE == ROW_FFT_W_RHS) {
+      a[t] = A.x[o0 + t];
+      b[t] = A.xref[o0 + t];
+    }
+  }
+  const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
+#pragma unroll
+  for (int t = 0; t < kRhoEPT; ++t) {
+    const size_t o = o0 + t;
     if constexpr (MODE == ROW_FFT_W_ADJ) {
-      A.dst[o] = z;
+      A.dst[o] = z[t];
     } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-      float2 pv = A.p[o];
+      float2 pv = a[t];
       if (A.pupd) {
-        const float2 rv = A.r[o];
-        pv = make_float2(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y));
+        pv = make_float2(fmaf(beta, pv.x, b[t].x), fmaf(beta, pv.y, b[t].y));
         const_cast<float2*>(A.p)[o] = pv;
       }
-      float2 q = make_float2(fmaf(A.alpha, pv.x, z.x), fmaf(A.alpha, pv.y, z.y));
+      const float2 q = make_float2(fmaf(A.alpha, pv.x, z[t].x), fmaf(A.alpha, pv.y, z[t].y));
       A.dst[o] = q;
       acc += pv.x * q.x + pv.y * q.y;
     } else {
-      float2 xv = A.x[o], xr = A.xref[o];
-      float2 b = make_float2(z.x - A.alpha * (xv.x - xr.x), z.y - A.alpha * (xv.y - xr.y));
-      A.r[o] = b;
-      A.pout[o] = b;
+      const float2 bb = make_float2(z[t].x - A.alpha * (a[t].x - b[t].x), z[t].y - A.alpha * (a[t].y - b[t].y));
+      A.r[o] = bb;
+      A.pout[o] = bb;
       A.dx[o] = make_float2(0.f, 0.f);
-      acc += b.x * b.x + b.y * b.y;
+      acc += bb.x * bb.x + bb.y * bb.y;
     }
   }
   return acc;
@@ -247,8 +306,8 @@ template <int N1, int N2, int MODE>
 __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs A) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
-  constexpr int N = S::N, TL = S::TL, E = S::E;
-  extern __shared__ float2 smem[];
+  constexpr int N = S::N, TL = S::TL, E = S::E, LANES = RowCfg<N1, N2>::LANES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   const int lane = threadIdx.x / TL, idx = threadIdx.x % TL;
   const int f = A.f, Wc = A.Wc;
@@ -262,15 +321,19 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
     }
   }
 
-  const int R = blockIdx.x * RowCfg<N1, N2>::LANES + lane;   // row of the stacked coil planes
+  const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
+  float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE;
+  const float2* twA = (const float2*)(smem_raw + L.tw);
+  const float2* twB = twA + N;
+  const int R0 = blockIdx.x * LANES;
+  const int R = R0 + lane;                                   // row of the stacked coil planes
   const bool active = R < A.nrows;
   const int e1 = R % N;
-  float2* sm = smem + lane * S::SM_LANE;
   const float rs = rsqrtf((float)N);
-  const float beta = (MODE == ROW_W_IFFT && A.pupd) ? cg_beta(A) : 0.f;
   float2 v[E];
 
-  // ---- load, layout A: thread a < N1 holds row elements a + N1*m
+  // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
+  float wv[T::load_compact ? 1 : N2];
   if (idx < N1) {
 #pragma unroll
     for (int m = 0; m < N2; ++m) {
@@ -281,23 +344,62 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
           if (in_omega(e2, N, f)) val = A.src[(size_t)R * Wc + to_compact(e2, N, f)];
         } else if constexpr (MODE == ROW_W_IFFT) {
           const size_t o = (size_t)R * N + e2;
-          float2 sv = A.src[o];
-          if (A.pupd) {            // p = r + beta p on the coil planes, written back for the later passes
+          val = A.src[o];
+          if (A.pupd) {
             const float2 rv = A.r[o];
-            sv = make_float2(fmaf(beta, sv.x, rv.x), fmaf(beta, sv.y, rv.y));
-            const_cast<float2*>(A.src)[o] = sv;
+            const float beta = cg_beta(A);
+            val = make_float2(fmaf(beta, val.x, rv.x), fmaf(beta, val.y, rv.y));
           }
-          val = cscale(sv, sobolev_w(e1, e2, A) * rs);
+          wv[m] = sobolev_w(e1, e2, A);
         } else {  // ROW_P_IFFT
-          val = A.mask[(size_t)e1 * N + e2] ? cscale(A.src[(size_t)R * N + e2], rs) : make_float2(0.f, 0.f);
+          const float2 sv = A.src[(size_t)R * N + e2];
+          val = A.mask[(size_t)e1 * N + e2] ? sv : make_float2(0.f, 0.f);
         }
       }
       v[m] = val;
     }
   }
 
+  // ---- staged side inputs and twiddles
+  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  for (int l = 0; l < LANES; ++l) {
+    const int Rl = R0 + l;
+    if (Rl >= A.nrows) break;
+    const int e1l = Rl % N;
+    if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
+    if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
+    if constexpr (MODE == ROW_FFT_RESID)
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
+    if constexpr (MODE == ROW_FFT_W_NORMAL)
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.p + (size_t)N * N + (size_t)Rl * N, N * 8);
+    if constexpr (MODE == ROW_FFT_W_RHS) {
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.x + (size_t)N * N + (size_t)Rl * N, N * 8);
+      stage_bytes(smem_raw + L.cplx + ((size_t)LANES + l) * N * 8, A.xref + (size_t)N * N + (size_t)Rl * N,
+                  N * 8);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  if constexpr (MODE == ROW_W_IFFT) {
+    // write back p = r + beta p, then weight
+    if (active && idx < N1) {
+#pragma unroll
+      for (int m = 0; m < N2; ++m) {
+        if (A.pupd) const_cast<float2*>(A.src)[(size_t)R * N + idx + N1 * m] = v[m];
+        v[m] = cscale(v[m], wv[m] * rs);
+      }
+    }
+  } else if constexpr (MODE == ROW_P_IFFT) {
+    if (idx < N1) {
+#pragma unroll
+      for (int m = 0; m < N2; ++m) v[m] = cscale(v[m], rs);
+    }
+  }
+
   if constexpr (T::inverse_first) {
-    fft_AtoB<N1, N2, +1>(v, sm, A.twA, idx);
+    fft_AtoB<N1, N2, +1>(v, sm, twA, idx);
     // layout B: thread b < N2 holds elements b + N2*m; keep the Omega columns
     if (active && idx < N2) {
 #pragma unroll
@@ -308,17 +410,17 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
     }
     return;
   } else {
-    fft_AtoB<N1, N2, -1>(v, sm, A.twA, idx);
+    fft_AtoB<N1, N2, -1>(v, sm, twA, idx);
+    const unsigned char* smask = smem_raw + L.mask + (size_t)lane * N;
     if constexpr (MODE == ROW_PSF) {
       if (idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-          const int e2 = idx + N2 * m;
-          const float s = (active && A.mask[(size_t)e1 * N + e2]) ? rs * rs : 0.f;
-          v[m] = cscale(v[m], s);
+          const float sc = (active && smask[idx + N2 * m]) ? rs * rs : 0.f;
+          v[m] = cscale(v[m], sc);
         }
       }
-      fft_AtoB<N2, N1, +1>(v, sm, A.twB, idx);
+      fft_AtoB<N2, N1, +1>(v, sm, twB, idx);
       if (active && idx < N1) {
 #pragma unroll
         for (int m = 0; m < N2; ++m) {
@@ -328,31 +430,34 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
       }
       return;
     } else {
+      const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
+      const float2* sc0 = (const float2*)(smem_raw + L.cplx) + (size_t)lane * N;
+      const float2* sc1 = (const float2*)(smem_raw + L.cplx) + ((size_t)LANES + lane) * N;
       if (active && idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
           const int e2 = idx + N2 * m;
           const size_t o = (size_t)R * N + e2;
           if constexpr (MODE == ROW_FFT_P_OUT) {
-            A.dst[o] = A.mask[(size_t)e1 * N + e2] ? cscale(v[m], rs) : make_float2(0.f, 0.f);
+            A.dst[o] = smask[e2] ? cscale(v[m], rs) : make_float2(0.f, 0.f);
           } else if constexpr (MODE == ROW_FFT_RESID) {
-            float2 yv = A.y[o];
-            float2 rv = A.mask[(size_t)e1 * N + e2] ? csub(yv, cscale(v[m], rs)) : yv;
+            const float2 yv = sc0[e2];
+            const float2 rv = smask[e2] ? csub(yv, cscale(v[m], rs)) : yv;
             A.dst[o] = rv;
             acc += rv.x * rv.x + rv.y * rv.y;
           } else {
-            const float2 val = cscale(v[m], sobolev_w(e1, e2, A) * rs);
-            const size_t oc = (size_t)A.N * A.N + o;      // coil planes follow the rho plane
+            const float2 val = cscale(v[m], sw[e2] * rs);
+            const size_t oc = (size_t)N * N + o;      // coil planes follow the rho plane
             if constexpr (MODE == ROW_FFT_W_ADJ) {
               A.dst[oc] = val;
             } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-              float2 pv = A.p[oc];
-              float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
+              const float2 pv = sc0[e2];
+              const float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
               A.dst[oc] = q;
               acc += pv.x * q.x + pv.y * q.y;
             } else {  // ROW_FFT_W_RHS
-              float2 xv = A.x[oc], xr = A.xref[oc];
-              float2 b = make_float2(val.x - A.alpha * (xv.x - xr.x), val.y - A.alpha * (xv.y - xr.y));
+              const float2 xv = sc0[e2], xr = sc1[e2];
+              const float2 b = make_float2(val.x - A.alpha * (xv.x - xr.x), val.y - A.alpha * (xv.y - xr.y));
               A.r[oc] = b;
               A.pout[oc] = b;
               A.dx[oc] = make_float2(0.f, 0.f);
@@ -376,48 +481,119 @@ enum ColMode : int {
   NUM_COL_MODES = 5
 };
 
+// Shared-memory layout of a column pass (byte offsets): exchange, twiddles, then `nside` side arrays of
+// Wc x C complex values (Omega rows of the block's columns: coil map, rho, drho, r).
+struct ColSmem {
+  size_t xch, tw, side, total;
+  int nside;
+};
+__host__ __device__ inline ColSmem col_smem(int mode, int N, int C, int sm_lane, int Wc) {
+  ColSmem L{};
+  L.nside = (mode == COL_IFFT_PROD_FFT) ? 4 : (mode == COL_IFFT_ADJ_FFT) ? 2 : 0;
+  L.xch = 0;
+  L.tw = align16((size_t)C * sm_lane * 8);
+  L.side = L.tw + align16((size_t)2 * N * 8);
+  L.total = L.side + (size_t)L.nside * Wc * C * 8;
+  return L;
+}
+
 template <int N1, int N2> struct ColCfg {
   using S = Split<N1, N2>;
-  static constexpr int C = 8;                       // adjacent compact columns per block
+  static constexpr int C = NLV_COL_C;               // adjacent compact columns per block
   static constexpr int THREADS = C * S::TL;
-  static constexpr size_t SMEM = (size_t)C * S::SM_LANE * sizeof(float2);
+  static_assert(C % 2 == 0, "column staging copies pairs of complex values");
 };
+
+// Stages Omega rows of C columns starting at compact column cc0 of a compact (Wc x Wc per coil) array.
+__device__ __forceinline__ void stage_compact_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc) {
+  const int cpr = C / 2;                               // 16-byte chunks per row segment
+  for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
+    const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
+    if (cc < Wc) cp_async16(sdst + (size_t)cr * C + 2 * k, plane + (size_t)cr * Wc + cc);
+  }
+}
+// Same for a natural N x N plane (rows and columns mapped from compact to natural indices).
+__device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc, int N,
+                                                   int f) {
+  if ((f & 1) == 0) {                                  // compact pairs (2k, 2k+1) stay adjacent in natural order
+    const int cpr = C / 2;
+    for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
+      const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
+      if (cc < Wc)
+        cp_async16(sdst + (size_t)cr * C + 2 * k,
+                   plane + (size_t)to_natural(cr, N, f) * N + to_natural(cc, N, f));
+    }
+  } else {
+    for (int i = threadIdx.x; i < Wc * C; i += blockDim.x) {
+      const int cr = i / C, k = i % C, cc = cc0 + k;
+      if (cc < Wc)
+        cp_async8(sdst + (size_t)cr * C + k, plane + (size_t)to_natural(cr, N, f) * N + to_natural(cc, N, f));
+    }
+  }
+}
 
 template <int N1, int N2, int MODE>
 __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
   const int f = A.f, Wc = A.Wc;
   const int strips = (Wc + C - 1) / C;
   const int j = blockIdx.x / strips;
-  const int cc = (blockIdx.x % strips) * C + lane;
+  const int cc0 = (blockIdx.x % strips) * C;
+  const int cc = cc0 + lane;
   const bool active = cc < Wc && j < A.nrows;
   const int x2 = to_natural(cc, N, f);
-  float2* sm = smem + lane * S::SM_LANE;
+  const ColSmem L = col_smem(MODE, N, C, S::SM_LANE, Wc);
+  float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE;
+  const float2* twA = (const float2*)(smem_raw + L.tw);
+  const float2* twB = twA + N;
+  const float2* side = (const float2*)(smem_raw + L.side);
   const float rs = rsqrtf((float)N);
   const size_t tbase = (size_t)j * N * Wc + cc;       // T element (row e1) at tbase + e1*Wc
   const size_t cbase = (size_t)j * Wc * Wc + cc;      // compact coil element (row cr) at cbase + cr*Wc
-  const float beta = (MODE == COL_IFFT_PROD_FFT && A.pupd) ? cg_beta(A) : 0.f;
   float2 v[E];
 
-  if constexpr (MODE == COL_PROD_FFT || MODE == COL_SIM_FFT) {
-    if (idx < N1) {
+  // ---- main loads, layout A: thread a < N1 holds column elements a + N1*m
+  if (idx < N1) {
 #pragma unroll
-      for (int m = 0; m < N2; ++m) {
-        const int e1 = idx + N1 * m;
-        float2 val = make_float2(0.f, 0.f);
+    for (int m = 0; m < N2; ++m) {
+      const int e1 = idx + N1 * m;
+      float2 val = make_float2(0.f, 0.f);
+      if constexpr (MODE == COL_PROD_FFT || MODE == COL_SIM_FFT) {
         if (active && in_omega(e1, N, f)) {
-          float2 c = (MODE == COL_PROD_FFT) ? A.coil[cbase + (size_t)to_compact(e1, N, f) * Wc]
-                                            : A.cimg[((size_t)j * N + e1) * N + x2];
+          const float2 c = (MODE == COL_PROD_FFT) ? A.coil[cbase + (size_t)to_compact(e1, N, f) * Wc]
+                                                  : A.cimg[((size_t)j * N + e1) * N + x2];
           val = cmul(A.rho[(size_t)e1 * N + x2], c);
         }
-        v[m] = val;
+      } else {
+        if (active) val = A.src[tbase + (size_t)e1 * Wc];
       }
+      v[m] = val;
     }
-    fft_AtoB<N1, N2, -1>(v, sm, A.twA, idx);
+  }
+  // ---- staged side inputs (Omega rows of this block's columns) and twiddles
+  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  if (j < A.nrows) {
+    float2* sd = (float2*)(smem_raw + L.side);
+    const size_t sstride = (size_t)Wc * C;
+    if constexpr (MODE == COL_IFFT_PROD_FFT || MODE == COL_IFFT_ADJ_FFT) {
+      stage_compact_cols(sd, A.coil + (size_t)j * Wc * Wc, cc0, C, Wc);
+      stage_natural_cols(sd + sstride, A.rho, cc0, C, Wc, N, f);
+    }
+    if constexpr (MODE == COL_IFFT_PROD_FFT) {
+      stage_natural_cols(sd + 2 * sstride, A.drho, cc0, C, Wc, N, f);
+      if (A.pupd) stage_natural_cols(sd + 3 * sstride, A.r, cc0, C, Wc, N, f);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  if constexpr (MODE == COL_PROD_FFT || MODE == COL_SIM_FFT) {
+    fft_AtoB<N1, N2, -1>(v, sm, twA, idx);
     if (active && idx < N2) {
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
@@ -427,14 +603,7 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
     }
     return;
   } else {
-    if (idx < N1) {
-#pragma unroll
-      for (int m = 0; m < N2; ++m) {
-        const int e1 = idx + N1 * m;
-        v[m] = active ? A.src[tbase + (size_t)e1 * Wc] : make_float2(0.f, 0.f);
-      }
-    }
-    fft_AtoB<N1, N2, +1>(v, sm, A.twA, idx);
+    fft_AtoB<N1, N2, +1>(v, sm, twA, idx);
     if constexpr (MODE == COL_IFFT_C) {
       if (active && idx < N2) {
 #pragma unroll
@@ -445,32 +614,34 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
       }
       return;
     } else {
+      const size_t sstride = (size_t)Wc * C;
+      const float beta = (MODE == COL_IFFT_PROD_FFT && A.pupd) ? cg_beta(A) : 0.f;
       if (idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
           const int e1 = idx + N2 * m;
           float2 out = make_float2(0.f, 0.f);
           if (active && in_omega(e1, N, f)) {
+            const int cr = to_compact(e1, N, f);
             const float2 u = cscale(v[m], rs);
-            const size_t on = (size_t)e1 * N + x2;
-            const float2 c = A.coil[cbase + (size_t)to_compact(e1, N, f) * Wc];
-            const float2 rh = A.rho[on];
+            const float2 c = side[(size_t)cr * C + lane];
+            const float2 rh = side[sstride + (size_t)cr * C + lane];
             if constexpr (MODE == COL_IFFT_PROD_FFT) {
-              float2 dr = A.drho[on];
+              float2 dr = side[2 * sstride + (size_t)cr * C + lane];
               if (A.pupd) {          // rho part of p = r + beta p (written later by the last row pass)
-                const float2 rv = A.r[on];
+                const float2 rv = side[3 * sstride + (size_t)cr * C + lane];
                 dr = make_float2(fmaf(beta, dr.x, rv.x), fmaf(beta, dr.y, rv.y));
               }
               out = cadd(cmul(dr, c), cmul(rh, u));
             } else {  // COL_IFFT_ADJ_FFT
-              A.zsum[cbase + (size_t)to_compact(e1, N, f) * Wc] = cmulc(c, u);
+              A.zsum[cbase + (size_t)cr * Wc] = cmulc(c, u);
               out = cmulc(rh, u);
             }
           }
           v[m] = out;
         }
       }
-      fft_AtoB<N2, N1, -1>(v, sm, A.twB, idx);
+      fft_AtoB<N2, N1, -1>(v, sm, twB, idx);
       if (active && idx < N1) {
 #pragma unroll
         for (int m = 0; m < N2; ++m) {
@@ -486,9 +657,12 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
 struct SizeKernels {
   int N1, N2;
   int row_lanes, row_threads, col_lanes, col_threads;
-  size_t row_smem, col_smem;
+  int sm_lane;              // shared float2 per lane for one exchange
   const void* row[NUM_ROW_MODES];
   const void* col[NUM_COL_MODES];
+  size_t row_smem(int mode) const { return row_smem_layout(mode).total; }
+  RowSmem row_smem_layout(int mode) const { return nlv::row_smem(mode, N1 * N2, row_lanes, sm_lane); }
+  size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane, Wc).total; }
 };
 
 template <int N1, int N2> SizeKernels make_size_kernels() {
@@ -497,10 +671,9 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.N2 = N2;
   s.row_lanes = RowCfg<N1, N2>::LANES;
   s.row_threads = RowCfg<N1, N2>::THREADS;
-  s.row_smem = RowCfg<N1, N2>::SMEM;
   s.col_lanes = ColCfg<N1, N2>::C;
   s.col_threads = ColCfg<N1, N2>::THREADS;
-  s.col_smem = ColCfg<N1, N2>::SMEM;
+  s.sm_lane = Split<N1, N2>::SM_LANE;
   s.row[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT>;
   s.row[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF>;
   s.row[ROW_FFT_P_OUT] = (const void*)row_pass<N1, N2, ROW_FFT_P_OUT>;

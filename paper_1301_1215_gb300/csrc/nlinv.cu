@@ -173,13 +173,13 @@ cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J * c->N;
   a.coil_blocks = row_blocks(c, false);
   void* args[] = {&a};
-  return launch(c, c->k->row[mode], row_blocks(c, rho), c->k->row_threads, c->k->row_smem, args);
+  return launch(c, c->k->row[mode], row_blocks(c, rho), c->k->row_threads, c->k->row_smem(mode), args);
 }
 
 cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J;
   void* args[] = {&a};
-  return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem, args);
+  return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
 }
 
 // c_j = W^-1 chat_j on Omega, for the coil planes of x (1+J planes).
@@ -422,13 +422,26 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "1") == 0;
   c->vec_blocks = std::max(1, sms) * 4;
 
-  // dynamic shared memory above the 48 KB default
-  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m)
-    if (c->k->row_smem > 48 * 1024)
-      cudaFuncSetAttribute(c->k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->k->row_smem);
-  for (int m = 0; m < nlv::NUM_COL_MODES; ++m)
-    if (c->k->col_smem > 48 * 1024)
-      cudaFuncSetAttribute(c->k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->k->col_smem);
+  // dynamic shared memory above the 48 KB default, within the device's opt-in limit
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  // (the limit is raised to the device maximum so that contexts with different fov can share the kernels)
+  size_t smem_max = 0;
+  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m) {
+    smem_max = std::max(smem_max, c->k->row_smem(m));
+    cudaFuncSetAttribute(c->k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  }
+  for (int m = 0; m < nlv::NUM_COL_MODES; ++m) {
+    smem_max = std::max(smem_max, c->k->col_smem(m, c->Wc));
+    cudaFuncSetAttribute(c->k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  }
+  if (smem_max > (size_t)smem_optin) {
+    g_create_error = "passes need " + std::to_string(smem_max) + " bytes of shared memory per block, the device allows " +
+                     std::to_string(smem_optin);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NLINV_EINVAL;
+  }
 
   // workspace layout
   const size_t cplx = sizeof(float2);

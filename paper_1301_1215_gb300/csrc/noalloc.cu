@@ -140,12 +140,12 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
     ds.l = p->sobolev_l;
   }
 
-  if (k->row_smem > 48 * 1024 || k->col_smem > 48 * 1024) {
-    for (int m : {nlv::ROW_W_IFFT, nlv::ROW_FFT_P_OUT})
-      cudaFuncSetAttribute(k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->row_smem);
-    for (int m : {nlv::COL_IFFT_C, nlv::COL_PROD_FFT})
-      cudaFuncSetAttribute(k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k->col_smem);
-  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  for (int m : {nlv::ROW_W_IFFT, nlv::ROW_FFT_P_OUT})
+    cudaFuncSetAttribute(k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  for (int m : {nlv::COL_IFFT_C, nlv::COL_PROD_FFT})
+    cudaFuncSetAttribute(k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
 
   // the same four passes as nlinv_forward, on the scratch array instead of a context workspace
   nlv::KArgs a{};
@@ -157,16 +157,16 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
 
   nlv::KArgs a1 = a;                        // T = FFT^-1_row(w chat_j), Omega columns
   a1.src = xv + plane; a1.dst = T; a1.nrows = J * N;
-  e = launch(k->row[nlv::ROW_W_IFFT], rows, k->row_threads, k->row_smem, st, a1);
+  e = launch(k->row[nlv::ROW_W_IFFT], rows, k->row_threads, k->row_smem(nlv::ROW_W_IFFT), st, a1);
   nlv::KArgs a2 = a;                        // c_j = Omega rows of FFT^-1_col(T)
   a2.src = T; a2.dst = coil; a2.nrows = J;
-  if (e == cudaSuccess) e = launch(k->col[nlv::COL_IFFT_C], cols, k->col_threads, k->col_smem, st, a2);
+  if (e == cudaSuccess) e = launch(k->col[nlv::COL_IFFT_C], cols, k->col_threads, k->col_smem(nlv::COL_IFFT_C, Wc), st, a2);
   nlv::KArgs a3 = a;                        // T = FFT_col(M rho c_j)
   a3.rho = xv; a3.coil = coil; a3.dst = T; a3.nrows = J;
-  if (e == cudaSuccess) e = launch(k->col[nlv::COL_PROD_FFT], cols, k->col_threads, k->col_smem, st, a3);
+  if (e == cudaSuccess) e = launch(k->col[nlv::COL_PROD_FFT], cols, k->col_threads, k->col_smem(nlv::COL_PROD_FFT, Wc), st, a3);
   nlv::KArgs a4 = a;                        // y = P FFT_row(T)
   a4.src = T; a4.dst = (float2*)y_out; a4.mask = mask; a4.nrows = J * N;
-  if (e == cudaSuccess) e = launch(k->row[nlv::ROW_FFT_P_OUT], rows, k->row_threads, k->row_smem, st, a4);
+  if (e == cudaSuccess) e = launch(k->row[nlv::ROW_FFT_P_OUT], rows, k->row_threads, k->row_smem(nlv::ROW_FFT_P_OUT), st, a4);
   if (e != cudaSuccess) return fail(NLINV_ECUDA, std::string("nlinv_forward_noalloc: ") + cudaGetErrorString(e));
   return NLINV_OK;
 }
