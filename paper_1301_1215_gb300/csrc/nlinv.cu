@@ -426,18 +426,24 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   // (the limit is raised to the device maximum so that contexts with different fov can share the kernels)
-  size_t smem_max = 0;
-  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m) {
-    smem_max = std::max(smem_max, c->k->row_smem(m));
-    cudaFuncSetAttribute(c->k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  }
-  for (int m = 0; m < nlv::NUM_COL_MODES; ++m) {
-    smem_max = std::max(smem_max, c->k->col_smem(m, c->Wc));
-    cudaFuncSetAttribute(c->k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  }
-  if (smem_max > (size_t)smem_optin) {
-    g_create_error = "passes need " + std::to_string(smem_max) + " bytes of shared memory per block, the device allows " +
-                     std::to_string(smem_optin);
+  std::string smem_err;
+  auto allow = [&](const void* fn, size_t need) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) { smem_err = "cudaFuncGetAttributes failed"; return; }
+    const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+    if ((size_t)dyn_max < need) {
+      smem_err = "a pass needs " + std::to_string(need) + " bytes of dynamic shared memory, the device allows " +
+                 std::to_string(dyn_max);
+      return;
+    }
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
+      smem_err = "cudaFuncSetAttribute failed";
+  };
+  for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) allow(c->k->row[m], c->k->row_smem(m));
+  for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) allow(c->k->col[m], c->k->col_smem(m, c->Wc));
+  if (!smem_err.empty()) {
+    cudaGetLastError();
+    g_create_error = smem_err;
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
     return NLINV_EINVAL;

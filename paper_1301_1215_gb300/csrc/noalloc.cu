@@ -142,10 +142,13 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
 
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  for (int m : {nlv::ROW_W_IFFT, nlv::ROW_FFT_P_OUT})
-    cudaFuncSetAttribute(k->row[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  for (int m : {nlv::COL_IFFT_C, nlv::COL_PROD_FFT})
-    cudaFuncSetAttribute(k->col[m], cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  for (const void* fn : {k->row[nlv::ROW_W_IFFT], k->row[nlv::ROW_FFT_P_OUT], k->col[nlv::COL_IFFT_C],
+                         k->col[nlv::COL_PROD_FFT]}) {
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess)
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
+  }
+  cudaGetLastError();
 
   // the same four passes as nlinv_forward, on the scratch array instead of a context workspace
   nlv::KArgs a{};
