@@ -206,26 +206,22 @@ template <int MODE> struct RowTraits {
   static constexpr bool reduces = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL || MODE == ROW_FFT_W_RHS);
   // side inputs staged per row: sampling-pattern row (bytes), weight row (floats), complex rows
   static constexpr bool s_mask = (MODE == ROW_PSF || MODE == ROW_FFT_P_OUT || MODE == ROW_FFT_RESID);
-  static constexpr bool s_w = has_rho;
-  static constexpr int s_cplx = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL) ? 1
-                              : (MODE == ROW_FFT_W_RHS) ? 2 : 0;
+  static constexpr bool s_w = has_rho || MODE == ROW_W_IFFT;
 };
 
 // Shared-memory layout of a row pass (byte offsets), identical on host and device.
 struct RowSmem {
-  size_t xch, tw, mask, w, cplx, total;
+  size_t xch, tw, mask, w, total;
 };
 __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_lane) {
   RowSmem L{};
   const bool m = (mode == ROW_PSF || mode == ROW_FFT_P_OUT || mode == ROW_FFT_RESID);
-  const bool w = (mode == ROW_FFT_W_ADJ || mode == ROW_FFT_W_NORMAL || mode == ROW_FFT_W_RHS);
-  const int nc = (mode == ROW_FFT_RESID || mode == ROW_FFT_W_NORMAL) ? 1 : (mode == ROW_FFT_W_RHS) ? 2 : 0;
+  const bool w = (mode == ROW_FFT_W_ADJ || mode == ROW_FFT_W_NORMAL || mode == ROW_FFT_W_RHS || mode == ROW_W_IFFT);
   L.xch = 0;
   L.tw = align16((size_t)lanes * sm_lane * 8);
   L.mask = L.tw + align16((size_t)2 * N * 8);
   L.w = L.mask + (m ? align16((size_t)lanes * N) : 0);
-  L.cplx = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
-  L.total = L.cplx + (size_t)nc * lanes * N * 8;
+  L.total = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
   return L;
 }
 
@@ -333,7 +329,6 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
   float2 v[E];
 
   // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
-  float wv[T::load_compact ? 1 : N2];
   if (idx < N1) {
 #pragma unroll
     for (int m = 0; m < N2; ++m) {
@@ -350,7 +345,6 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
             const float beta = cg_beta(A);
             val = make_float2(fmaf(beta, val.x, rv.x), fmaf(beta, val.y, rv.y));
           }
-          wv[m] = sobolev_w(e1, e2, A);
         } else {  // ROW_P_IFFT
           const float2 sv = A.src[(size_t)R * N + e2];
           val = A.mask[(size_t)e1 * N + e2] ? sv : make_float2(0.f, 0.f);
@@ -369,26 +363,18 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
     const int e1l = Rl % N;
     if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
     if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
-    if constexpr (MODE == ROW_FFT_RESID)
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
-    if constexpr (MODE == ROW_FFT_W_NORMAL)
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.p + (size_t)N * N + (size_t)Rl * N, N * 8);
-    if constexpr (MODE == ROW_FFT_W_RHS) {
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.x + (size_t)N * N + (size_t)Rl * N, N * 8);
-      stage_bytes(smem_raw + L.cplx + ((size_t)LANES + l) * N * 8, A.xref + (size_t)N * N + (size_t)Rl * N,
-                  N * 8);
-    }
   }
   cp_async_wait_all();
   __syncthreads();
 
   if constexpr (MODE == ROW_W_IFFT) {
     // write back p = r + beta p, then weight
+    const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
     if (active && idx < N1) {
 #pragma unroll
       for (int m = 0; m < N2; ++m) {
         if (A.pupd) const_cast<float2*>(A.src)[(size_t)R * N + idx + N1 * m] = v[m];
-        v[m] = cscale(v[m], wv[m] * rs);
+        v[m] = cscale(v[m], sw[idx + N1 * m] * rs);
       }
     }
   } else if constexpr (MODE == ROW_P_IFFT) {
@@ -431,8 +417,21 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
       return;
     } else {
       const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
-      const float2* sc0 = (const float2*)(smem_raw + L.cplx) + (size_t)lane * N;
-      const float2* sc1 = (const float2*)(smem_raw + L.cplx) + ((size_t)LANES + lane) * N;
+      // per-row vectors of the output step, loaded into registers before the first store
+      constexpr int NV = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL) ? 1 : (MODE == ROW_FFT_W_RHS) ? 2 : 0;
+      float2 a0[NV ? N1 : 1], a1[NV == 2 ? N1 : 1];
+      if (NV && active && idx < N2) {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+          const size_t o = (size_t)R * N + idx + N2 * m, oc = (size_t)N * N + o;
+          if constexpr (MODE == ROW_FFT_RESID) a0[m] = A.y[o];
+          if constexpr (MODE == ROW_FFT_W_NORMAL) a0[m] = A.p[oc];
+          if constexpr (MODE == ROW_FFT_W_RHS) {
+            a0[m] = A.x[oc];
+            a1[m] = A.xref[oc];
+          }
+        }
+      }
       if (active && idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
@@ -441,7 +440,7 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
           if constexpr (MODE == ROW_FFT_P_OUT) {
             A.dst[o] = smask[e2] ? cscale(v[m], rs) : make_float2(0.f, 0.f);
           } else if constexpr (MODE == ROW_FFT_RESID) {
-            const float2 yv = sc0[e2];
+            const float2 yv = a0[m];
             const float2 rv = smask[e2] ? csub(yv, cscale(v[m], rs)) : yv;
             A.dst[o] = rv;
             acc += rv.x * rv.x + rv.y * rv.y;
@@ -451,12 +450,12 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
             if constexpr (MODE == ROW_FFT_W_ADJ) {
               A.dst[oc] = val;
             } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-              const float2 pv = sc0[e2];
+              const float2 pv = a0[m];
               const float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
               A.dst[oc] = q;
               acc += pv.x * q.x + pv.y * q.y;
             } else {  // ROW_FFT_W_RHS
-              const float2 xv = sc0[e2], xr = sc1[e2];
+              const float2 xv = a0[m], xr = a1[m];
               const float2 b = make_float2(val.x - A.alpha * (xv.x - xr.x), val.y - A.alpha * (xv.y - xr.y));
               A.r[oc] = b;
               A.pout[oc] = b;
