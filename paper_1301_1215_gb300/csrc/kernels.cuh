@@ -41,7 +41,8 @@ struct Scalars {
 struct KArgs {
   int N, J, f, Wc;          // grid side, coils, half-width of Omega, compact width 2f
   int nrows;                // row passes: rows of the coil planes (J*N); column passes: J
-  int coil_blocks;          // row passes with a rho part: blocks that work on coil rows
+  int rows_per_cta;         // row passes: consecutive coil rows handled by one block
+  int rho_per_cta;          // row passes with a rho part: consecutive rho-plane pixels handled by one block
   const float* wtab;        // Sobolev weight w(k) = (1 + a |k|^2)^(-l/2), N x N natural order
   float alpha;              // alpha_n of Eq. 3 for the normal operator and the right-hand side
   int pupd;                 // CG passes: first form p = r + beta p (beta from Scalars) and write it back
@@ -225,70 +226,61 @@ __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_l
   return L;
 }
 
-#ifndef NLV_ROW_THREADS
-#define NLV_ROW_THREADS 256
-#endif
 #ifndef NLV_COL_C
 #define NLV_COL_C 8
 #endif
 
-template <int N1, int N2> struct RowCfg {
-  using S = Split<N1, N2>;
-  static constexpr int LANES = (NLV_ROW_THREADS / S::TL) >= 16 ? 16 : (NLV_ROW_THREADS / S::TL) >= 8 ? 8
-                             : (NLV_ROW_THREADS / S::TL) >= 4 ? 4 : (NLV_ROW_THREADS / S::TL) >= 2 ? 2 : 1;
-  static constexpr int THREADS = LANES * S::TL;
-};
+// Row passes run kRowCtasPerSM blocks per SM; a block holds up to kRowMaxThreads threads (whole lanes of TL
+// threads) and loops over its share of rows when they do not fit at once.
+constexpr int kRowMaxThreads = 320;
+constexpr int kRowCtasPerSM = 2;
 
 // rho plane of the adjoint / normal / right-hand-side outputs: the sum of the channel products over the coils on
-// Omega (the channel summation of Table 1) plus the mode's alpha term.  Each thread takes kRhoEPT consecutive
-// pixels of one row; all loads are issued before the first store.
-constexpr int kRhoEPT = 8;
-
+// Omega (the channel summation of Table 1) plus the mode's alpha term.  Every block takes an equal slice of the
+// plane after its rows, all of its threads working on it; each thread issues its loads before its stores.
 template <int MODE>
-__device__ __forceinline__ float rho_part(const KArgs& A, int rb) {
+__device__ __forceinline__ float rho_slice(const KArgs& A) {
   const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
-  const long first = ((long)rb * blockDim.x + threadIdx.x) * kRhoEPT;
-  float acc = 0.f;
-  if (first >= (long)N * N) return acc;
-  const int e1 = (int)(first / N), e20 = (int)(first % N);
-  const bool row_in = in_omega(e1, N, f);
-  const int cr = to_compact(e1, N, f);
-  const size_t o0 = (size_t)e1 * N + e20;
-  float2 z[kRhoEPT], a[kRhoEPT], b[kRhoEPT];
-#pragma unroll
-  for (int t = 0; t < kRhoEPT; ++t) {
-    const int e2 = e20 + t;
-    z[t] = make_float2(0.f, 0.f);
-    if (row_in && in_omega(e2, N, f)) {
-      const float2* zp = A.zsum + (size_t)cr * Wc + to_compact(e2, N, f);
-      const size_t stride = (size_t)Wc * Wc;
-      for (int j = 0; j < J; ++j) z[t] = cadd(z[t], zp[j * stride]);
-    }
-    if constexpr (MODE == ROW_FFT_W_NORMAL) {
-      a[t] = A.p[o0 + t];
-      b[t] = A.pupd ? A.r[o0 + t] : make_float2(0.f, 0.f);
-    } else if constexpr (MODE == ROW_FFT_W_RHS) {
-      a[t] = A.x[o0 + t];
-      b[t] = A.xref[o0 + t];
-    }
-  }
+  const long plane = (long)N * N;
+  const long e_begin = (long)blockIdx.x * A.rho_per_cta;
+  const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
   const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
-#pragma unroll
-  for (int t = 0; t < kRhoEPT; ++t) {
-    const size_t o = o0 + t;
+  float acc = 0.f;
+  for (long o = e_begin + threadIdx.x; o < e_end; o += blockDim.x) {
+    const int e1 = (int)(o / N), e2 = (int)(o % N);
+    float2 z = make_float2(0.f, 0.f), a = z, b = z;
+    if constexpr (MODE == ROW_FFT_W_NORMAL) {
+      a = A.p[o];
+      if (A.pupd) b = A.r[o];
+    } else if constexpr (MODE == ROW_FFT_W_RHS) {
+      a = A.x[o];
+      b = A.xref[o];
+    }
+    if (in_omega(e1, N, f) && in_omega(e2, N, f)) {
+      const float2* zp = A.zsum + (size_t)to_compact(e1, N, f) * Wc + to_compact(e2, N, f);
+      const size_t stride = (size_t)Wc * Wc;
+      float2 z0 = z, z1 = z;
+      int j = 0;
+      for (; j + 2 <= J; j += 2) {
+        z0 = cadd(z0, zp[j * stride]);
+        z1 = cadd(z1, zp[(j + 1) * stride]);
+      }
+      if (j < J) z0 = cadd(z0, zp[j * stride]);
+      z = cadd(z0, z1);
+    }
     if constexpr (MODE == ROW_FFT_W_ADJ) {
-      A.dst[o] = z[t];
+      A.dst[o] = z;
     } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-      float2 pv = a[t];
+      float2 pv = a;
       if (A.pupd) {
-        pv = make_float2(fmaf(beta, pv.x, b[t].x), fmaf(beta, pv.y, b[t].y));
+        pv = make_float2(fmaf(beta, pv.x, b.x), fmaf(beta, pv.y, b.y));
         const_cast<float2*>(A.p)[o] = pv;
       }
-      const float2 q = make_float2(fmaf(A.alpha, pv.x, z[t].x), fmaf(A.alpha, pv.y, z[t].y));
+      const float2 q = make_float2(fmaf(A.alpha, pv.x, z.x), fmaf(A.alpha, pv.y, z.y));
       A.dst[o] = q;
       acc += pv.x * q.x + pv.y * q.y;
     } else {
-      const float2 bb = make_float2(z[t].x - A.alpha * (a[t].x - b[t].x), z[t].y - A.alpha * (a[t].y - b[t].y));
+      const float2 bb = make_float2(z.x - A.alpha * (a.x - b.x), z.y - A.alpha * (a.y - b.y));
       A.r[o] = bb;
       A.pout[o] = bb;
       A.dx[o] = make_float2(0.f, 0.f);
@@ -298,34 +290,34 @@ __device__ __forceinline__ float rho_part(const KArgs& A, int rb) {
   return acc;
 }
 
+// Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
+// (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
+// plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
 template <int N1, int N2, int MODE>
-__global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs A) {
+__global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
-  constexpr int N = S::N, TL = S::TL, E = S::E, LANES = RowCfg<N1, N2>::LANES;
+  constexpr int N = S::N, TL = S::TL, E = S::E;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
+  const int LANES = blockDim.x / TL;
   const int lane = threadIdx.x / TL, idx = threadIdx.x % TL;
   const int f = A.f, Wc = A.Wc;
   float acc = 0.f;
-
-  if constexpr (T::has_rho) {
-    if ((int)blockIdx.x >= A.coil_blocks) {
-      acc = rho_part<MODE>(A, (int)blockIdx.x - A.coil_blocks);
-      if constexpr (T::reduces) grid_reduce(acc, A);
-      return;
-    }
-  }
-
   const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
   float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE;
   const float2* twA = (const float2*)(smem_raw + L.tw);
   const float2* twB = twA + N;
-  const int R0 = blockIdx.x * LANES;
-  const int R = R0 + lane;                                   // row of the stacked coil planes
-  const bool active = R < A.nrows;
-  const int e1 = R % N;
   const float rs = rsqrtf((float)N);
+  const int r_begin = blockIdx.x * A.rows_per_cta;
+  const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
+  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+
+  for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
+  const int R = R0 + lane;                                   // row of the stacked coil planes
+  const bool active = R < r_end;
+  const int e1 = R % N;
   float2 v[E];
 
   // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
@@ -354,12 +346,10 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
     }
   }
 
-  // ---- staged side inputs and twiddles
-  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
-  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  // ---- staged side inputs (the twiddles were issued before the first round)
   for (int l = 0; l < LANES; ++l) {
     const int Rl = R0 + l;
-    if (Rl >= A.nrows) break;
+    if (Rl >= r_end) break;
     const int e1l = Rl % N;
     if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
     if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
@@ -394,7 +384,6 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
         if (in_omega(e2, N, f)) A.dst[(size_t)R * Wc + to_compact(e2, N, f)] = v[m];
       }
     }
-    return;
   } else {
     fft_AtoB<N1, N2, -1>(v, sm, twA, idx);
     const unsigned char* smask = smem_raw + L.mask + (size_t)lane * N;
@@ -414,7 +403,6 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
           if (in_omega(e2, N, f)) A.dst[(size_t)R * Wc + to_compact(e2, N, f)] = v[m];
         }
       }
-      return;
     } else {
       const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
       // per-row vectors of the output step, loaded into registers before the first store
@@ -465,9 +453,13 @@ __global__ void __launch_bounds__(RowCfg<N1, N2>::THREADS) row_pass(const KArgs 
           }
         }
       }
-      if constexpr (T::reduces) grid_reduce(acc, A);
     }
   }
+  __syncthreads();       // the next round restages the side rows
+  }  // rounds
+
+  if constexpr (T::has_rho) acc += rho_slice<MODE>(A);
+  if constexpr (T::reduces) grid_reduce(acc, A);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----
@@ -655,21 +647,39 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
 // ------------------------------------------------------------------------------- per-size kernel table ----
 struct SizeKernels {
   int N1, N2;
-  int row_lanes, row_threads, col_lanes, col_threads;
+  int tl;                   // threads per lane
+  int col_lanes, col_threads;
   int sm_lane;              // shared float2 per lane for one exchange
   const void* row[NUM_ROW_MODES];
   const void* col[NUM_COL_MODES];
-  size_t row_smem(int mode) const { return row_smem_layout(mode).total; }
-  RowSmem row_smem_layout(int mode) const { return nlv::row_smem(mode, N1 * N2, row_lanes, sm_lane); }
+  size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
   size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane, Wc).total; }
 };
+
+// Launch geometry of a row pass: `blocks` blocks of `lanes` lanes, each taking rows_per_cta rows (and rho_per_cta
+// pixels of the rho plane when the pass has one), so that the rows are split evenly over ctas_per_sm blocks per SM.
+struct RowGrid {
+  int blocks, lanes, rows_per_cta, rho_per_cta;
+};
+inline RowGrid row_grid(const SizeKernels* k, int nrows, long rho_pixels, int sms, int ctas_per_sm) {
+  RowGrid g{};
+  const int max_lanes = kRowMaxThreads / k->tl;
+  int want = sms * ctas_per_sm;
+  if (want > nrows) want = nrows;
+  const int per = (nrows + want - 1) / want;
+  const int rounds = (per + max_lanes - 1) / max_lanes;
+  g.lanes = (per + rounds - 1) / rounds;
+  g.rows_per_cta = per;
+  g.blocks = (nrows + per - 1) / per;
+  g.rho_per_cta = (int)((rho_pixels + g.blocks - 1) / g.blocks);
+  return g;
+}
 
 template <int N1, int N2> SizeKernels make_size_kernels() {
   SizeKernels s{};
   s.N1 = N1;
   s.N2 = N2;
-  s.row_lanes = RowCfg<N1, N2>::LANES;
-  s.row_threads = RowCfg<N1, N2>::THREADS;
+  s.tl = Split<N1, N2>::TL;
   s.col_lanes = ColCfg<N1, N2>::C;
   s.col_threads = ColCfg<N1, N2>::THREADS;
   s.sm_lane = Split<N1, N2>::SM_LANE;

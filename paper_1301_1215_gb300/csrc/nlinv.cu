@@ -77,6 +77,8 @@ struct nlinv_ctx {
   bool own_stream = false;
   int device = 0;
   int vec_blocks = 0;         // grid of the vector kernels
+  int sms = 0;                // streaming multiprocessors of the device
+  int row_ctas_per_sm = nlv::kRowCtasPerSM;   // blocks per SM of the row passes
   // workspace (one allocation)
   void* base = nullptr;
   float2 *x = nullptr, *xref = nullptr, *y = nullptr, *r0 = nullptr;
@@ -136,14 +138,8 @@ KArgs base_args(const nlinv_ctx* c) {
   return a;
 }
 
-int row_blocks(const nlinv_ctx* c, bool with_rho) {
-  const int L = c->k->row_lanes;
-  int b = (c->J * c->N + L - 1) / L;
-  if (with_rho) {
-    const long per = (long)c->k->row_threads * nlv::kRhoEPT;
-    b += (int)((c->plane + per - 1) / per);
-  }
-  return b;
+nlv::RowGrid row_geom(const nlinv_ctx* c, bool with_rho) {
+  return nlv::row_grid(c->k, c->J * c->N, with_rho ? c->plane : 0, c->sms, c->row_ctas_per_sm);
 }
 
 int col_blocks(const nlinv_ctx* c) {
@@ -170,10 +166,12 @@ cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t sme
 
 cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
   const bool rho = (mode == nlv::ROW_FFT_W_ADJ || mode == nlv::ROW_FFT_W_NORMAL || mode == nlv::ROW_FFT_W_RHS);
+  const nlv::RowGrid g = row_geom(c, rho);
   a.nrows = c->J * c->N;
-  a.coil_blocks = row_blocks(c, false);
+  a.rows_per_cta = g.rows_per_cta;
+  a.rho_per_cta = g.rho_per_cta;
   void* args[] = {&a};
-  return launch(c, c->k->row[mode], row_blocks(c, rho), c->k->row_threads, c->k->row_smem(mode), args);
+  return launch(c, c->k->row[mode], g.blocks, g.lanes * c->k->tl, c->k->row_smem(mode, g.lanes), args);
 }
 
 cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
@@ -420,7 +418,8 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "1") == 0;
-  c->vec_blocks = std::max(1, sms) * 4;
+  c->sms = std::max(1, sms);
+  c->vec_blocks = c->sms * 4;
 
   // dynamic shared memory above the 48 KB default, within the device's opt-in limit
   int smem_optin = 0;
@@ -439,7 +438,9 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess)
       smem_err = "cudaFuncSetAttribute failed";
   };
-  for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) allow(c->k->row[m], c->k->row_smem(m));
+  const int lanes_max = std::max(row_geom(c, false).lanes, row_geom(c, true).lanes);
+  for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m)
+    allow(c->k->row[m], c->k->row_smem(m, lanes_max));
   for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) allow(c->k->col[m], c->k->col_smem(m, c->Wc));
   if (!smem_err.empty()) {
     cudaGetLastError();
@@ -457,7 +458,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   const size_t twb = align_up((size_t)c->N * cplx, 256);
   const size_t wb = align_up((size_t)c->plane * sizeof(float), 256);
   const size_t maskb = align_up((size_t)c->plane, 256);
-  const int max_blocks = std::max(row_blocks(c, true), c->vec_blocks);
+  const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
   const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + partb + scb;

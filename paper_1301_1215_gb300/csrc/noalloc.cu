@@ -154,13 +154,15 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   nlv::KArgs a{};
   a.N = N; a.J = J; a.f = f; a.Wc = Wc;
   a.wtab = wtab; a.twA = twA; a.twB = twB;
-  const int rows = (J * N + k->row_lanes - 1) / k->row_lanes;
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const nlv::RowGrid rg = nlv::row_grid(k, J * N, 0, sms < 1 ? 1 : sms, nlv::kRowCtasPerSM);
   const int cols = J * ((Wc + k->col_lanes - 1) / k->col_lanes);
   const float2* xv = (const float2*)x;
 
   nlv::KArgs a1 = a;                        // T = FFT^-1_row(w chat_j), Omega columns
-  a1.src = xv + plane; a1.dst = T; a1.nrows = J * N;
-  e = launch(k->row[nlv::ROW_W_IFFT], rows, k->row_threads, k->row_smem(nlv::ROW_W_IFFT), st, a1);
+  a1.src = xv + plane; a1.dst = T; a1.nrows = J * N; a1.rows_per_cta = rg.rows_per_cta;
+  e = launch(k->row[nlv::ROW_W_IFFT], rg.blocks, rg.lanes * k->tl, k->row_smem(nlv::ROW_W_IFFT, rg.lanes), st, a1);
   nlv::KArgs a2 = a;                        // c_j = Omega rows of FFT^-1_col(T)
   a2.src = T; a2.dst = coil; a2.nrows = J;
   if (e == cudaSuccess) e = launch(k->col[nlv::COL_IFFT_C], cols, k->col_threads, k->col_smem(nlv::COL_IFFT_C, Wc), st, a2);
@@ -168,8 +170,10 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   a3.rho = xv; a3.coil = coil; a3.dst = T; a3.nrows = J;
   if (e == cudaSuccess) e = launch(k->col[nlv::COL_PROD_FFT], cols, k->col_threads, k->col_smem(nlv::COL_PROD_FFT, Wc), st, a3);
   nlv::KArgs a4 = a;                        // y = P FFT_row(T)
-  a4.src = T; a4.dst = (float2*)y_out; a4.mask = mask; a4.nrows = J * N;
-  if (e == cudaSuccess) e = launch(k->row[nlv::ROW_FFT_P_OUT], rows, k->row_threads, k->row_smem(nlv::ROW_FFT_P_OUT), st, a4);
+  a4.src = T; a4.dst = (float2*)y_out; a4.mask = mask; a4.nrows = J * N; a4.rows_per_cta = rg.rows_per_cta;
+  if (e == cudaSuccess)
+    e = launch(k->row[nlv::ROW_FFT_P_OUT], rg.blocks, rg.lanes * k->tl, k->row_smem(nlv::ROW_FFT_P_OUT, rg.lanes), st,
+               a4);
   if (e != cudaSuccess) return fail(NLINV_ECUDA, std::string("nlinv_forward_noalloc: ") + cudaGetErrorString(e));
   return NLINV_OK;
 }
