@@ -36,6 +36,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--write-traffic", metavar="NCU_REP",
+                    help="read the DRAM bytes of the CG kernels from an ncu report of paper_1301_1215_gb300.profile_cg "
+                         "and write profiles/traffic.json (no GPU needed)")
     return ap.parse_args()
 
 
@@ -362,8 +365,35 @@ def synth_workload():
     return synth.WORKLOADS[WORKLOAD]
 
 
+CG_KERNEL_ORDER = ("row p-update/W^-1", "col W^-1/C/FFT", "row PSF", "col FFT^-1/C^H/FFT", "row W^-H+alpha p",
+                   "cg step")
+
+
+def write_traffic(rep: str) -> None:
+    """profiles/traffic.json from an ncu report holding, in launch order, the CG kernels of one
+    nlinv_profile_cg iteration (dram__bytes_read.sum + dram__bytes_write.sum per launch)."""
+    import csv
+    import io
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], capture_output=True, text=True, check=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    ri, wi = hdr.index("dram__bytes_read.sum"), hdr.index("dram__bytes_write.sum")
+    kernels = {}
+    for name, d in zip(CG_KERNEL_ORDER, data):
+        kernels[name] = int(float(d[ri]) * scale[units[ri]] + float(d[wi]) * scale[units[wi]])
+    doc = {"csrc_digest": csrc_digest(), "source": os.path.basename(rep), "kernels": kernels,
+           "note": "ncu flushes caches per replay pass: DRAM bytes of one cold launch"}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(doc, f, indent=1)
+    print(json.dumps(doc))
+
+
 def main():
     args = parse()
+    if args.write_traffic:
+        write_traffic(args.write_traffic)
+        return
     rank, world, local = dist_env()
     if world > 1:
         import torch

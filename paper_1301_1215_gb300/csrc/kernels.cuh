@@ -25,7 +25,6 @@ enum Reduce : int {
 };
 
 constexpr int kMaxNewton = 64;
-constexpr int kMaxGroups = 4;   // coil groups of the CG passes that run as concurrent branches
 
 // Scalars of the CG and Newton iterations, kept in device memory (FP64).
 struct Scalars {

@@ -78,9 +78,6 @@ struct nlinv_ctx {
   int device = 0;
   int vec_blocks = 0;         // grid of the vector kernels
   int sms = 0;                // streaming multiprocessors of the device
-  int groups = 2;             // coil groups whose per-coil passes run as concurrent graph branches
-  cudaStream_t aux[nlv::kMaxGroups] = {};   // branch streams (aux[0] unused: group 0 runs on `stream`)
-  cudaEvent_t ev_fork = nullptr, ev_join[nlv::kMaxGroups] = {};
   int row_ctas_per_sm = nlv::kRowCtasPerSM;   // blocks per SM of the row passes
   // workspace (one allocation)
   void* base = nullptr;
@@ -97,7 +94,7 @@ struct nlinv_ctx {
   long graph_launches = 0;
   long launches = 0;
   bool have_state = false;    // a reconstruction has filled the workspace
-  bool pdl = false;           // programmatic dependent launches (NLINV_PDL=1 turns them on; slower here)
+  bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   std::string err;
 };
@@ -150,25 +147,21 @@ int col_blocks(const nlinv_ctx* c) {
   return c->J * ((c->Wc + C - 1) / C);
 }
 
-// Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh) when it is switched on; measured
-// on the 384 x 384, 10-coil series it slowed each frame down (16.1 -> 18.6 ms), so it is off by default.
-cudaError_t launch_on(nlinv_ctx* c, cudaStream_t st, const void* fn, int grid, int block, size_t smem, void** args) {
+// Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh): the next pass is scheduled while
+// the current one drains (about 1% per frame on the 384 x 384, 10-coil series).
+cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
   c->launches++;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
+  cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = c->pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelExC(&cfg, fn, args);
-}
-
-cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
-  return launch_on(c, c->stream, fn, grid, block, smem, args);
 }
 
 cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
@@ -185,24 +178,6 @@ cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J;
   void* args[] = {&a};
   return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
-}
-
-// A row pass without a rho part over the coils [j0, j0 + nj) (the caller offsets the per-coil pointers), sized
-// for its share of the SMs, on stream st.
-cudaError_t row_sub(nlinv_ctx* c, cudaStream_t st, int mode, KArgs a, int nj, int sm_share) {
-  const nlv::RowGrid g = nlv::row_grid(c->k, nj * c->N, 0, sm_share, c->row_ctas_per_sm);
-  a.nrows = nj * c->N;
-  a.rows_per_cta = g.rows_per_cta;
-  void* args[] = {&a};
-  return launch_on(c, st, c->k->row[mode], g.blocks, g.lanes * c->k->tl, c->k->row_smem(mode, g.lanes), args);
-}
-
-cudaError_t col_sub(nlinv_ctx* c, cudaStream_t st, int mode, KArgs a, int nj) {
-  a.nrows = nj;
-  void* args[] = {&a};
-  const int C = c->k->col_lanes;
-  return launch_on(c, st, c->k->col[mode], nj * ((c->Wc + C - 1) / C), c->k->col_threads,
-                   c->k->col_smem(mode, c->Wc), args);
 }
 
 // c_j = W^-1 chat_j on Omega, for the coil planes of x (1+J planes).
@@ -260,61 +235,30 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
 //   K2 col  drho = r_rho + beta p_rho; T = FFT_col(M (drho c_j + rho W^-1 p_c))
 //   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> -> alpha
 //   K6      dx += alpha p, r -= alpha q, |r|^2 -> beta
-// K1..K4 for the coils [j0, j0 + nj) on stream st (they touch only those coils' planes).
-cudaError_t q_coil_chain(nlinv_ctx* c, cudaStream_t st, const float2* x, int j0, int nj, int sm_share) {
-  const size_t full = (size_t)j0 * c->plane, tofs = (size_t)j0 * c->N * c->Wc, cofs = (size_t)j0 * c->Wc * c->Wc;
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   KArgs a = base_args(c);
-  a.src = c->p + c->plane + full;
-  a.r = c->r + c->plane + full;
+  a.src = c->p + c->plane;
+  a.r = c->r + c->plane;
   a.pupd = 1;
-  a.dst = c->T + tofs;
-  cudaError_t e = row_sub(c, st, nlv::ROW_W_IFFT, a, nj, sm_share);
+  a.dst = c->T;
+  cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
   if (e != cudaSuccess) return e;
   a = base_args(c);
-  a.src = c->T + tofs;
-  a.dst = c->T + tofs;
+  a.src = c->T;
+  a.dst = c->T;
   a.rho = x;
   a.drho = c->p;
   a.r = c->r;
   a.pupd = 1;
-  a.coil = c->coil + cofs;
-  if ((e = col_sub(c, st, nlv::COL_IFFT_PROD_FFT, a, nj)) != cudaSuccess) return e;
+  a.coil = c->coil;
+  if ((e = col(c, nlv::COL_IFFT_PROD_FFT, a)) != cudaSuccess) return e;
   a = base_args(c);
-  a.src = c->T + tofs;
-  a.dst = c->T + tofs;
+  a.src = c->T;
+  a.dst = c->T;
   a.mask = c->mask;
-  if ((e = row_sub(c, st, nlv::ROW_PSF, a, nj, sm_share)) != cudaSuccess) return e;
+  if ((e = row(c, nlv::ROW_PSF, a)) != cudaSuccess) return e;
+  if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
   a = base_args(c);
-  a.src = c->T + tofs;
-  a.dst = c->T + tofs;
-  a.rho = x;
-  a.coil = c->coil + cofs;
-  a.zsum = c->zsum + cofs;
-  return col_sub(c, st, nlv::COL_IFFT_ADJ_FFT, a, nj);
-}
-
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
-  cudaError_t e = cudaSuccess;
-  const int G = std::min(c->groups, c->J);
-  if (G <= 1) {
-    e = q_coil_chain(c, c->stream, x, 0, c->J, c->sms);
-  } else {
-    // fork: the coil groups' chains run as concurrent branches, joined before the coil-summing pass
-    if ((e = cudaEventRecord(c->ev_fork, c->stream)) != cudaSuccess) return e;
-    for (int g = 1; g < G; ++g)
-      if ((e = cudaStreamWaitEvent(c->aux[g], c->ev_fork, 0)) != cudaSuccess) return e;
-    const int share = (c->sms + G - 1) / G;
-    for (int g = 0; g < G && e == cudaSuccess; ++g) {
-      const int j0 = (int)((long)c->J * g / G), j1 = (int)((long)c->J * (g + 1) / G);
-      e = q_coil_chain(c, g == 0 ? c->stream : c->aux[g], x, j0, j1 - j0, share);
-    }
-    for (int g = 1; g < G && e == cudaSuccess; ++g) {
-      if ((e = cudaEventRecord(c->ev_join[g], c->aux[g])) != cudaSuccess) return e;
-      e = cudaStreamWaitEvent(c->stream, c->ev_join[g], 0);
-    }
-  }
-  if (e != cudaSuccess) return e;
-  KArgs a = base_args(c);
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
@@ -473,19 +417,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "1") == 0;
-  if (const char* v = std::getenv("NLINV_COIL_GROUPS")) c->groups = std::max(1, std::min(nlv::kMaxGroups, std::atoi(v)));
-  for (int g = 1; g < c->groups && e == cudaSuccess; ++g) e = cudaStreamCreateWithFlags(&c->aux[g], cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-  for (int g = 1; g < c->groups && e == cudaSuccess; ++g) e = cudaEventCreateWithFlags(&c->ev_join[g], cudaEventDisableTiming);
-  if (e != cudaSuccess) {
-    g_create_error = std::string("stream/event set-up: ") + cudaGetErrorString(e);
-    for (int g = 1; g < nlv::kMaxGroups; ++g) { if (c->aux[g]) cudaStreamDestroy(c->aux[g]); if (c->ev_join[g]) cudaEventDestroy(c->ev_join[g]); }
-    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-    if (c->own_stream) cudaStreamDestroy(c->stream);
-    delete c;
-    return NLINV_ECUDA;
-  }
+  if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "0") != 0;
   c->sms = std::max(1, sms);
   c->vec_blocks = c->sms * 4;
 
@@ -598,11 +530,6 @@ nlinv_status nlinv_destroy(nlinv_ctx* c) {
   if (!c) return NLINV_OK;
   cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  for (int g = 1; g < nlv::kMaxGroups; ++g) {
-    if (c->aux[g]) { cudaStreamSynchronize(c->aux[g]); cudaStreamDestroy(c->aux[g]); }
-    if (c->ev_join[g]) cudaEventDestroy(c->ev_join[g]);
-  }
-  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   cudaFree(c->base);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
