@@ -192,6 +192,9 @@ template <int A, int B> struct Split {
   static constexpr int SM_AB = N2 * (N1 + 1);
   static constexpr int SM_BA = N1 * (N2 + 1);
   static constexpr int SM_LANE = (SM_AB > SM_BA ? SM_AB : SM_BA);
+  // lane stride for passes whose adjacent threads belong to adjacent lanes (column passes): padded to 2 mod 16
+  // float2 so that 8 lanes x 2 indices of a half-warp fall on distinct 8-byte banks
+  static constexpr int SM_LANE_COL = SM_LANE + ((2 - SM_LANE % 16) + 16) % 16;
 };
 
 // Layout A(P1, P2) -> layout B(P1, P2) for one lane of P1*P2 points.

@@ -212,7 +212,7 @@ template <int MODE> struct RowTraits {
 
 // Shared-memory layout of a row pass (byte offsets), identical on host and device.
 struct RowSmem {
-  size_t xch, tw, mask, w, total;
+  size_t xch, tw, mask, w, cplx, total;
 };
 __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_lane) {
   RowSmem L{};
@@ -222,7 +222,8 @@ __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_l
   L.tw = align16((size_t)lanes * sm_lane * 8);
   L.mask = L.tw + align16((size_t)2 * N * 8);
   L.w = L.mask + (m ? align16((size_t)lanes * N) : 0);
-  L.total = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
+  L.cplx = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
+  L.total = L.cplx + ((mode == ROW_FFT_RESID || mode == ROW_FFT_W_NORMAL) ? (size_t)lanes * N * 8 : 0);
   return L;
 }
 
@@ -353,6 +354,10 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
     const int e1l = Rl % N;
     if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
     if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
+    if constexpr (MODE == ROW_FFT_RESID)
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
+    if constexpr (MODE == ROW_FFT_W_NORMAL)
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.p + (size_t)N * N + (size_t)Rl * N, N * 8);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -405,19 +410,16 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
       }
     } else {
       const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
-      // per-row vectors of the output step, loaded into registers before the first store
-      constexpr int NV = (MODE == ROW_FFT_RESID || MODE == ROW_FFT_W_NORMAL) ? 1 : (MODE == ROW_FFT_W_RHS) ? 2 : 0;
-      float2 a0[NV ? N1 : 1], a1[NV == 2 ? N1 : 1];
+      // staged rows (y or p) and, for the right-hand side, x and x_ref loaded into registers before any store
+      const float2* scp = (const float2*)(smem_raw + L.cplx) + (size_t)lane * N;
+      constexpr int NV = (MODE == ROW_FFT_W_RHS) ? 2 : 0;
+      float2 a0[NV ? N1 : 1], a1[NV ? N1 : 1];
       if (NV && active && idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-          const size_t o = (size_t)R * N + idx + N2 * m, oc = (size_t)N * N + o;
-          if constexpr (MODE == ROW_FFT_RESID) a0[m] = A.y[o];
-          if constexpr (MODE == ROW_FFT_W_NORMAL) a0[m] = A.p[oc];
-          if constexpr (MODE == ROW_FFT_W_RHS) {
-            a0[m] = A.x[oc];
-            a1[m] = A.xref[oc];
-          }
+          const size_t oc = (size_t)N * N + (size_t)R * N + idx + N2 * m;
+          a0[m] = A.x[oc];
+          a1[m] = A.xref[oc];
         }
       }
       if (active && idx < N2) {
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
           if constexpr (MODE == ROW_FFT_P_OUT) {
             A.dst[o] = smask[e2] ? cscale(v[m], rs) : make_float2(0.f, 0.f);
           } else if constexpr (MODE == ROW_FFT_RESID) {
-            const float2 yv = a0[m];
+            const float2 yv = scp[e2];
             const float2 rv = smask[e2] ? csub(yv, cscale(v[m], rs)) : yv;
             A.dst[o] = rv;
             acc += rv.x * rv.x + rv.y * rv.y;
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
             if constexpr (MODE == ROW_FFT_W_ADJ) {
               A.dst[oc] = val;
             } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-              const float2 pv = a0[m];
+              const float2 pv = scp[e2];
               const float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
               A.dst[oc] = q;
               acc += pv.x * q.x + pv.y * q.y;
@@ -537,8 +539,8 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
   const int cc = cc0 + lane;
   const bool active = cc < Wc && j < A.nrows;
   const int x2 = to_natural(cc, N, f);
-  const ColSmem L = col_smem(MODE, N, C, S::SM_LANE, Wc);
-  float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE;
+  const ColSmem L = col_smem(MODE, N, C, S::SM_LANE_COL, Wc);
+  float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE_COL;
   const float2* twA = (const float2*)(smem_raw + L.tw);
   const float2* twB = twA + N;
   const float2* side = (const float2*)(smem_raw + L.side);
@@ -649,11 +651,12 @@ struct SizeKernels {
   int N1, N2;
   int tl;                   // threads per lane
   int col_lanes, col_threads;
-  int sm_lane;              // shared float2 per lane for one exchange
+  int sm_lane;              // shared float2 per lane for one exchange (row passes)
+  int sm_lane_col;          // the same for column passes (bank-conflict padding)
   const void* row[NUM_ROW_MODES];
   const void* col[NUM_COL_MODES];
   size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
-  size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane, Wc).total; }
+  size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane_col, Wc).total; }
 };
 
 // Launch geometry of a row pass: `blocks` blocks of `lanes` lanes, each taking rows_per_cta rows (and rho_per_cta
@@ -683,6 +686,7 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.col_lanes = ColCfg<N1, N2>::C;
   s.col_threads = ColCfg<N1, N2>::THREADS;
   s.sm_lane = Split<N1, N2>::SM_LANE;
+  s.sm_lane_col = Split<N1, N2>::SM_LANE_COL;
   s.row[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT>;
   s.row[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF>;
   s.row[ROW_FFT_P_OUT] = (const void*)row_pass<N1, N2, ROW_FFT_P_OUT>;
