@@ -223,7 +223,7 @@ __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_l
   L.mask = L.tw + align16((size_t)2 * N * 8);
   L.w = L.mask + (m ? align16((size_t)lanes * N) : 0);
   L.cplx = L.w + (w ? align16((size_t)lanes * N * 4) : 0);
-  L.total = L.cplx + ((mode == ROW_FFT_RESID || mode == ROW_FFT_W_NORMAL) ? (size_t)lanes * N * 8 : 0);
+  L.total = L.cplx + ((mode == ROW_FFT_RESID) ? (size_t)lanes * N * 8 : 0);
   return L;
 }
 
@@ -356,8 +356,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
     if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
     if constexpr (MODE == ROW_FFT_RESID)
       stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
-    if constexpr (MODE == ROW_FFT_W_NORMAL)
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.p + (size_t)N * N + (size_t)Rl * N, N * 8);
   }
   cp_async_wait_all();
   __syncthreads();
@@ -410,16 +408,19 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
       }
     } else {
       const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
-      // staged rows (y or p) and, for the right-hand side, x and x_ref loaded into registers before any store
+      // staged rows of y; p, or x and x_ref, loaded into registers before any store
       const float2* scp = (const float2*)(smem_raw + L.cplx) + (size_t)lane * N;
-      constexpr int NV = (MODE == ROW_FFT_W_RHS) ? 2 : 0;
-      float2 a0[NV ? N1 : 1], a1[NV ? N1 : 1];
+      constexpr int NV = (MODE == ROW_FFT_W_RHS) ? 2 : (MODE == ROW_FFT_W_NORMAL) ? 1 : 0;
+      float2 a0[NV ? N1 : 1], a1[NV == 2 ? N1 : 1];
       if (NV && active && idx < N2) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
           const size_t oc = (size_t)N * N + (size_t)R * N + idx + N2 * m;
-          a0[m] = A.x[oc];
-          a1[m] = A.xref[oc];
+          if constexpr (MODE == ROW_FFT_W_NORMAL) a0[m] = A.p[oc];
+          if constexpr (MODE == ROW_FFT_W_RHS) {
+            a0[m] = A.x[oc];
+            a1[m] = A.xref[oc];
+          }
         }
       }
       if (active && idx < N2) {
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
             if constexpr (MODE == ROW_FFT_W_ADJ) {
               A.dst[oc] = val;
             } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-              const float2 pv = scp[e2];
+              const float2 pv = a0[m];
               const float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
               A.dst[oc] = q;
               acc += pv.x * q.x + pv.y * q.y;
