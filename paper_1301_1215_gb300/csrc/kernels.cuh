@@ -16,20 +16,21 @@
 namespace nlv {
 
 // ------------------------------------------------------------------------------------------ arguments ----
-// Last-block reductions (passes that run once per Newton step or per operator call); the CG loop itself uses the
-// deferred partials of KArgs::part_out.
 enum Reduce : int {
   RED_NONE = 0,       // the block partials are summed into Scalars::last
   RED_RESID = 1,      // Scalars::resid[slot] = sqrt(sum)       (|y - F x_n|)
+  RED_RR_INIT = 2,    // Scalars::rr = sum                      (|b|^2 at the start of CG)
+  RED_PQ = 3,         // Scalars::alpha = rr / sum              (sum = Re<p, A p>)
+  RED_RR_UPDATE = 4,  // Scalars::beta = sum / rr, rr = sum     (|r_new|^2)
 };
 
 constexpr int kMaxNewton = 64;
 
 // Scalars of the CG and Newton iterations, kept in device memory (FP64).
 struct Scalars {
-  double rr;                     // |r|^2 of the last CG step's residual
-  double alpha;                  // last CG step length
-  double beta;                   // (unused by the deferred CG scalars)
+  double rr;                     // |r|^2 of the current CG residual
+  double alpha;                  // CG step length
+  double beta;                   // CG direction update
   double pq;                     // last Re<p, A p>
   double last;                   // result of a RED_NONE reduction
   double resid[kMaxNewton + 1];  // |y - F x_n| per Newton step
@@ -62,19 +63,10 @@ struct KArgs {
   float2* dx;               // CG solution, (1+J) planes
   const float2* twA;        // twiddles of the split (N1, N2)
   const float2* twB;        // twiddles of the split (N2, N1)
-  double* partials;         // one double per block (last-block reductions)
+  double* partials;         // one double per block
   Scalars* sc;
   int reduce;               // Reduce
   int slot;                 // RED_RESID index
-  // Deferred reductions of the CG loop: a producer writes one FP64 partial per block into part_out (no fence, no
-  // atomic); consumers sum the partial arrays at their start, in the same order in every block, to form
-  // beta = |r_i|^2 / |r_{i-1}|^2 and alpha = |r_i|^2 / Re<p_i, A p_i>.
-  double* part_out;
-  const double* rr_cur;     // partials of |r_i|^2
-  const double* rr_prev;    // partials of |r_{i-1}|^2
-  const double* pq;         // partials of Re<p_i, A p_i>
-  int n_rr_cur, n_rr_prev, n_pq;
-  int beta_zero;            // first CG iteration of a Newton step: beta = 0
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -97,6 +89,8 @@ __device__ __forceinline__ float sobolev_w(int k1, int k2, const KArgs& A) {
   return __ldg(&A.wtab[(size_t)k1 * A.N + k2]);
 }
 
+// beta of the pending direction update p = r + beta p (CG, Table 1)
+__device__ __forceinline__ float cg_beta(const KArgs& A) { return (float)A.sc->beta; }
 
 // ----------------------------------------------------------------------------------------- reductions ----
 __device__ __forceinline__ double warp_sum(double v) {
@@ -120,37 +114,26 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// Sum of n partials in a fixed order (the same in every block); every thread of the block must call it and gets
-// the result.
-__device__ __forceinline__ double sum_partials(const double* p, int n) {
-  __shared__ double red[32];
-  __shared__ double result;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += p[i];
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) result = s;
-  __syncthreads();
-  return result;
-}
-
-// beta of the pending direction update p = r + beta p (CG, Table 1).  All threads must call it.
-__device__ __forceinline__ float cg_beta(const KArgs& A) {
-  if (A.beta_zero) return 0.f;
-  const double rn = sum_partials(A.rr_cur, A.n_rr_cur);
-  const double ro = sum_partials(A.rr_prev, A.n_rr_prev);
-  return ro != 0.0 ? (float)(rn / ro) : 0.f;
-}
-
-// This block's partial of a deferred reduction.
-__device__ __forceinline__ void write_partial(float mine, const KArgs& A) {
-  __shared__ double red[32];
-  const double s = block_sum((double)mine, red);
-  if (threadIdx.x == 0) A.part_out[blockIdx.x] = s;
-}
-
 __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slot, double total) {
   switch (reduce) {
     case RED_RESID: sc->resid[slot] = sqrt(total); break;
+    case RED_RR_INIT: sc->rr = total; sc->beta = 0.0; break;
+    case RED_PQ: {
+      // The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 (or |r|^2 = 0) only occurs once CG has
+      // reached the rounding floor: the step is then empty.  Non-finite values are a breakdown.
+      double rr = sc->rr, a = 0.0;
+      sc->pq = total;
+      if (!isfinite(total) || !isfinite(rr)) sc->flags |= 1;
+      else if (rr != 0.0 && total > 0.0) a = rr / total;
+      sc->alpha = a;
+      break;
+    }
+    case RED_RR_UPDATE: {
+      double rr = sc->rr;
+      sc->beta = (rr != 0.0) ? total / rr : 0.0;
+      sc->rr = total;
+      break;
+    }
     default: sc->last = total; break;
   }
 }
@@ -257,11 +240,12 @@ constexpr int kRowCtasPerSM = 2;
 // Omega (the channel summation of Table 1) plus the mode's alpha term.  Every block takes an equal slice of the
 // plane after its rows, all of its threads working on it; each thread issues its loads before its stores.
 template <int MODE>
-__device__ __forceinline__ float rho_slice(const KArgs& A, float beta) {
+__device__ __forceinline__ float rho_slice(const KArgs& A) {
   const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
   const long plane = (long)N * N;
   const long e_begin = (long)blockIdx.x * A.rho_per_cta;
   const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
+  const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
   float acc = 0.f;
   for (long o = e_begin + threadIdx.x; o < e_end; o += blockDim.x) {
     const int e1 = (int)(o / N), e2 = (int)(o % N);
@@ -330,7 +314,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
-  const float beta = ((MODE == ROW_W_IFFT || MODE == ROW_FFT_W_NORMAL) && A.pupd) ? cg_beta(A) : 0.f;
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int R = R0 + lane;                                   // row of the stacked coil planes
@@ -352,6 +335,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
           val = A.src[o];
           if (A.pupd) {
             const float2 rv = A.r[o];
+            const float beta = cg_beta(A);
             val = make_float2(fmaf(beta, val.x, rv.x), fmaf(beta, val.y, rv.y));
           }
         } else {  // ROW_P_IFFT
@@ -477,11 +461,8 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   __syncthreads();       // the next round restages the side rows
   }  // rounds
 
-  if constexpr (T::has_rho) acc += rho_slice<MODE>(A, beta);
-  if constexpr (T::reduces) {
-    if (A.part_out) write_partial(acc, A);
-    else grid_reduce(acc, A);
-  }
+  if constexpr (T::has_rho) acc += rho_slice<MODE>(A);
+  if constexpr (T::reduces) grid_reduce(acc, A);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----

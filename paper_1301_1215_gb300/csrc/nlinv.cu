@@ -32,22 +32,11 @@ namespace {
 thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
-// alpha = |r|^2 / Re<p, A p> from the deferred partials (0 at the rounding floor; a non-finite value is a
-// breakdown), then dx += alpha p; r -= alpha q; partials of |r|^2.   n2 = number of complex pairs (float4).
+// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.   n2 = number of complex pairs (float4 accesses).
 __global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, const float4* __restrict__ q4,
                                float4* __restrict__ r4, float4* __restrict__ dx4, long n2) {
   nlv::pdl_enter();
-  const double rr = nlv::sum_partials(A.rr_cur, A.n_rr_cur);
-  const double pq = nlv::sum_partials(A.pq, A.n_pq);
-  const bool bad = !isfinite(rr) || !isfinite(pq);
-  const double ad = (!bad && rr != 0.0 && pq > 0.0) ? rr / pq : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    A.sc->rr = rr;
-    A.sc->pq = pq;
-    A.sc->alpha = ad;
-    if (bad) atomicOr(&A.sc->flags, 1);
-  }
-  const float a = (float)ad;
+  const float a = (float)A.sc->alpha;
   float acc = 0.f;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
     float4 p = p4[i], q = q4[i], r = r4[i], d = dx4[i];
@@ -57,7 +46,7 @@ __global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, con
     r4[i] = r;
     acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
   }
-  nlv::write_partial(acc, A);
+  nlv::grid_reduce(acc, A);
 }
 
 // x += dx
@@ -99,10 +88,6 @@ struct nlinv_ctx {
   float* wtab = nullptr;      // Sobolev weight, N x N
   uint8_t* mask = nullptr;
   double* partials = nullptr;
-  double* part_pq = nullptr;          // deferred partials of Re<p, A p>
-  double* part_rr[2] = {nullptr, nullptr};   // deferred partials of |r|^2, alternating between iterations
-  int n_part_rhs = 0;                 // blocks of the right-hand-side pass (partials it writes)
-  int n_part_pq = 0;                  // blocks of the normal-operator row pass
   Scalars* sc = nullptr;
   // graph of one reconstruction
   cudaGraphExec_t graph = nullptr;
@@ -250,19 +235,8 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
 //   K2 col  drho = r_rho + beta p_rho; T = FFT_col(M (drho c_j + rho W^-1 p_c))
 //   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> -> alpha
 //   K6      dx += alpha p, r -= alpha q, |r|^2 -> beta
-// Deferred-scalar wiring of CG iteration i: |r_i|^2 partials in part_rr[i % 2] (written by the right-hand side for
-// i = 0, by the CG step of iteration i-1 otherwise), |r_{i-1}|^2 in the other buffer.
-void cg_wire(const nlinv_ctx* c, KArgs& a, int i) {
-  a.rr_cur = c->part_rr[i % 2];
-  a.n_rr_cur = (i == 0) ? c->n_part_rhs : c->vec_blocks;
-  a.rr_prev = c->part_rr[(i + 1) % 2];
-  a.n_rr_prev = (i <= 1) ? c->n_part_rhs : c->vec_blocks;
-  a.beta_zero = (i == 0);
-}
-
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, int i) {
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   KArgs a = base_args(c);
-  cg_wire(c, a, i);
   a.src = c->p + c->plane;
   a.r = c->r + c->plane;
   a.pupd = 1;
@@ -270,7 +244,6 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, int i) {
   cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
   if (e != cudaSuccess) return e;
   a = base_args(c);
-  cg_wire(c, a, i);
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -286,7 +259,6 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, int i) {
   if ((e = row(c, nlv::ROW_PSF, a)) != cudaSuccess) return e;
   if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
   a = base_args(c);
-  cg_wire(c, a, i);
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
@@ -294,13 +266,10 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, int i) {
   a.pupd = 1;
   a.zsum = c->zsum;
   a.alpha = alpha;
-  a.part_out = c->part_pq;
+  a.reduce = nlv::RED_PQ;
   if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
   a = base_args(c);
-  cg_wire(c, a, i);
-  a.pq = c->part_pq;
-  a.n_pq = c->n_part_pq;
-  a.part_out = c->part_rr[(i + 1) % 2];
+  a.reduce = nlv::RED_RR_UPDATE;
   const long n2 = c->vec / 2;
   const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
   float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
@@ -347,10 +316,10 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     a.pout = c->p;
     a.dx = c->dx;
     a.alpha = al;
-    a.part_out = c->part_rr[0];
+    a.reduce = nlv::RED_RR_INIT;
     if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
     for (int i = 0; i < P.cg_iters; ++i)
-      if ((e = q_cg_iter(c, c->x, al, i)) != cudaSuccess) return e;
+      if ((e = q_cg_iter(c, c->x, al)) != cudaSuccess) return e;
     const long n2 = c->vec / 2;
     const float4* d4 = (const float4*)c->dx;
     float4* x4 = (float4*)c->x;
@@ -492,7 +461,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
-  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 4 * partb + scb;
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + partb + scb;
   e = cudaMalloc(&c->base, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -519,11 +488,6 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   c->wtab = (float*)take(wb);
   c->mask = (uint8_t*)take(maskb);
   c->partials = (double*)take(partb);
-  c->part_pq = (double*)take(partb);
-  c->part_rr[0] = (double*)take(partb);
-  c->part_rr[1] = (double*)take(partb);
-  c->n_part_rhs = row_geom(c, true).blocks;
-  c->n_part_pq = row_geom(c, true).blocks;
   c->sc = (Scalars*)take(scb);
 
   // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
@@ -784,16 +748,15 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   const long n2 = c->vec / 2;
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < reps && e == cudaSuccess; ++it) {
-    const int i = 2 + it;                 // wiring of a later CG iteration: both |r|^2 buffers from CG steps
     int k = 0;
     auto mark = [&]() { if (e == cudaSuccess) e = cudaEventRecord(ev[k++], c->stream); };
     mark();
-    KArgs a = base_args(c); cg_wire(c, a, i);
+    KArgs a = base_args(c);
     a.src = c->p + c->plane; a.r = c->r + c->plane; a.pupd = 1; a.dst = c->T;
     if (e == cudaSuccess) e = row(c, nlv::ROW_W_IFFT, a);
     mark();
-    a = base_args(c); cg_wire(c, a, i);
-    a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.r = c->r; a.pupd = 1; a.coil = c->coil;
+    a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.r = c->r; a.pupd = 1;
+    a.coil = c->coil;
     if (e == cudaSuccess) e = col(c, nlv::COL_IFFT_PROD_FFT, a);
     mark();
     a = base_args(c); a.src = c->T; a.dst = c->T; a.mask = c->mask;
@@ -801,28 +764,26 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     mark();
     if (e == cudaSuccess) e = q_adj_col(c, c->x);
     mark();
-    a = base_args(c); cg_wire(c, a, i);
-    a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum; a.alpha = al;
-    a.part_out = c->part_pq;
+    a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum;
+    a.alpha = al; a.reduce = nlv::RED_PQ;
     if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
     mark();
-    a = base_args(c); cg_wire(c, a, i);
-    a.pq = c->part_pq; a.n_pq = c->n_part_pq; a.part_out = c->part_rr[(i + 1) % 2];
+    a = base_args(c); a.reduce = nlv::RED_RR_UPDATE;
     const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
     float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
     void* args1[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
     if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args1);
     mark();
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
-    for (int j = 0; j < K && e == cudaSuccess; ++j) {
+    for (int i = 0; i < K && e == cudaSuccess; ++i) {
       float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[j], ev[j + 1]);
-      acc[j] += ms;
+      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      acc[i] += ms;
     }
   }
-  for (int j = 0; j <= K; ++j) cudaEventDestroy(ev[j]);
+  for (int i = 0; i <= K; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return cuda_fail(c, e, "nlinv_profile_cg");
-  for (int j = 0; j < K; ++j) ms_out[j] = acc[j] / reps;
+  for (int i = 0; i < K; ++i) ms_out[i] = acc[i] / reps;
   return NLINV_OK;
 }
 
