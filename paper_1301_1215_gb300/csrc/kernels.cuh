@@ -67,7 +67,6 @@ struct KArgs {
   Scalars* sc;
   int reduce;               // Reduce
   int slot;                 // RED_RESID index
-  int part_early;           // normal-operator pass: publish the block's partial before its stores when possible
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -136,34 +135,6 @@ __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slo
       break;
     }
     default: sc->last = total; break;
-  }
-}
-
-// Two halves of grid_reduce for passes that hold their outputs in registers: the block publishes its partial
-// before issuing its stores (so the gpu-scope fence does not wait for them to drain), stores, then the last block
-// finishes.  Every thread must call both.
-__device__ __forceinline__ bool grid_reduce_begin(float mine, const KArgs& A) {
-  __shared__ double red[32];
-  __shared__ bool last;
-  const double s = block_sum((double)mine, red);
-  if (threadIdx.x == 0) {
-    A.partials[blockIdx.x] = s;
-    __threadfence();
-    const unsigned t = atomicAdd(&A.sc->ticket, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  return last;
-}
-__device__ __forceinline__ void grid_reduce_finish(const KArgs& A) {
-  __shared__ double red[32];
-  __threadfence();
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(&A.partials[i]);
-  const double total = block_sum(acc, red);
-  if (threadIdx.x == 0) {
-    finalize_scalar(A.sc, A.reduce, A.slot, total);
-    A.sc->ticket = 0u;
   }
 }
 
@@ -323,60 +294,6 @@ __device__ __forceinline__ float rho_slice(const KArgs& A) {
 // Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
-// The rho-plane slice of the normal operator with its outputs kept in registers (at most kRhoHold pixels per
-// thread), for the single-round path that publishes Re<p, q> before storing.
-constexpr int kRhoHold = 4;
-struct RhoHold {
-  float2 p[kRhoHold], q[kRhoHold];
-};
-__device__ __forceinline__ float rho_slice_hold(const KArgs& A, RhoHold& h) {
-  const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
-  const long plane = (long)N * N;
-  const long e_begin = (long)blockIdx.x * A.rho_per_cta;
-  const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
-  const float beta = A.pupd ? cg_beta(A) : 0.f;
-  float acc = 0.f;
-#pragma unroll
-  for (int t = 0; t < kRhoHold; ++t) {
-    const long o = e_begin + threadIdx.x + (long)t * blockDim.x;
-    if (o >= e_end) continue;
-    const int e1 = (int)(o / N), e2 = (int)(o % N);
-    float2 pv = A.p[o];
-    const float2 rv = A.pupd ? A.r[o] : make_float2(0.f, 0.f);
-    float2 z = make_float2(0.f, 0.f);
-    if (in_omega(e1, N, f) && in_omega(e2, N, f)) {
-      const float2* zp = A.zsum + (size_t)to_compact(e1, N, f) * Wc + to_compact(e2, N, f);
-      const size_t stride = (size_t)Wc * Wc;
-      float2 z0 = z, z1 = z;
-      int j = 0;
-      for (; j + 2 <= J; j += 2) {
-        z0 = cadd(z0, zp[j * stride]);
-        z1 = cadd(z1, zp[(j + 1) * stride]);
-      }
-      if (j < J) z0 = cadd(z0, zp[j * stride]);
-      z = cadd(z0, z1);
-    }
-    if (A.pupd) pv = make_float2(fmaf(beta, pv.x, rv.x), fmaf(beta, pv.y, rv.y));
-    const float2 q = make_float2(fmaf(A.alpha, pv.x, z.x), fmaf(A.alpha, pv.y, z.y));
-    h.p[t] = pv;
-    h.q[t] = q;
-    acc += pv.x * q.x + pv.y * q.y;
-  }
-  return acc;
-}
-__device__ __forceinline__ void rho_slice_store(const KArgs& A, const RhoHold& h) {
-  const long plane = (long)A.N * A.N;
-  const long e_begin = (long)blockIdx.x * A.rho_per_cta;
-  const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
-#pragma unroll
-  for (int t = 0; t < kRhoHold; ++t) {
-    const long o = e_begin + threadIdx.x + (long)t * blockDim.x;
-    if (o >= e_end) continue;
-    if (A.pupd) const_cast<float2*>(A.p)[o] = h.p[t];
-    A.dst[o] = h.q[t];
-  }
-}
-
 template <int N1, int N2, int MODE>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
   using S = Split<N1, N2>;
@@ -395,9 +312,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   const float rs = rsqrtf((float)N);
   const int r_begin = blockIdx.x * A.rows_per_cta;
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
-  // normal operator with one round and a small rho slice: publish Re<p, q> before the stores
-  const bool early = MODE == ROW_FFT_W_NORMAL && A.part_early && r_end - r_begin <= LANES &&
-                     A.rho_per_cta <= kRhoHold * (int)blockDim.x;
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
 
@@ -529,8 +443,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
             } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
               const float2 pv = a0[m];
               const float2 q = make_float2(fmaf(A.alpha, pv.x, val.x), fmaf(A.alpha, pv.y, val.y));
-              if (early) v[m] = q;            // stored after the block has published Re<p, q>
-              else A.dst[oc] = q;
+              A.dst[oc] = q;
               acc += pv.x * q.x + pv.y * q.y;
             } else {  // ROW_FFT_W_RHS
               const float2 xv = a0[m], xr = a1[m];
@@ -541,21 +454,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
               acc += b.x * b.x + b.y * b.y;
             }
           }
-        }
-      }
-      if constexpr (MODE == ROW_FFT_W_NORMAL) {
-        if (early) {
-          // single round: the rho slice too, then publish the block's Re<p, q>, then store everything
-          RhoHold h;
-          acc += rho_slice_hold(A, h);
-          const bool last = grid_reduce_begin(acc, A);
-          if (active && idx < N2) {
-#pragma unroll
-            for (int m = 0; m < N1; ++m) A.dst[(size_t)N * N + (size_t)R * N + idx + N2 * m] = v[m];
-          }
-          rho_slice_store(A, h);
-          if (last) grid_reduce_finish(A);
-          return;
         }
       }
     }

@@ -32,41 +32,21 @@ namespace {
 thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
-// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.  Each block takes kVecEPT consecutive groups of blockDim
-// float4 (two complex values each), holds the results in registers, publishes its partial of |r|^2 and then
-// stores, so that the gpu-scope fence of the reduction does not wait for the stores.  n2 = number of float4.
-constexpr int kVecEPT = 4;
-__global__ void __launch_bounds__(256) cg_step_kernel(const KArgs A, const float4* __restrict__ p4,
-                                                      const float4* __restrict__ q4, float4* __restrict__ r4,
-                                                      float4* __restrict__ dx4, long n2) {
+// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.   n2 = number of complex pairs (float4 accesses).
+__global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, const float4* __restrict__ q4,
+                               float4* __restrict__ r4, float4* __restrict__ dx4, long n2) {
   nlv::pdl_enter();
   const float a = (float)A.sc->alpha;
-  const long base = (long)blockIdx.x * blockDim.x * kVecEPT + threadIdx.x;
-  float4 rv[kVecEPT], dv[kVecEPT];
   float acc = 0.f;
-#pragma unroll
-  for (int u = 0; u < kVecEPT; ++u) {
-    const long i = base + (long)u * blockDim.x;
-    if (i < n2) {
-      const float4 p = p4[i], q = q4[i];
-      float4 r = r4[i], d = dx4[i];
-      d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
-      r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
-      rv[u] = r;
-      dv[u] = d;
-      acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-    }
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+    float4 p = p4[i], q = q4[i], r = r4[i], d = dx4[i];
+    d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
+    r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
+    dx4[i] = d;
+    r4[i] = r;
+    acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
   }
-  const bool last = nlv::grid_reduce_begin(acc, A);
-#pragma unroll
-  for (int u = 0; u < kVecEPT; ++u) {
-    const long i = base + (long)u * blockDim.x;
-    if (i < n2) {
-      r4[i] = rv[u];
-      dx4[i] = dv[u];
-    }
-  }
-  if (last) nlv::grid_reduce_finish(A);
+  nlv::grid_reduce(acc, A);
 }
 
 // x += dx
@@ -80,7 +60,6 @@ __global__ void add_kernel(const float4* __restrict__ d4, float4* __restrict__ x
 }
 
 constexpr int kVecThreads = 256;
-int cg_step_blocks(long n2) { return (int)((n2 + (long)kVecThreads * kVecEPT - 1) / ((long)kVecThreads * kVecEPT)); }
 constexpr int kProfileKernels = 6;   // kernels of one CG iteration, in the order nlinv_profile_cg reports them
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -288,7 +267,6 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   a.zsum = c->zsum;
   a.alpha = alpha;
   a.reduce = nlv::RED_PQ;
-  a.part_early = 1;
   if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
   a = base_args(c);
   a.reduce = nlv::RED_RR_UPDATE;
@@ -296,7 +274,7 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
   float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
   void* args[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
-  return launch(c, (const void*)cg_step_kernel, cg_step_blocks(n2), kVecThreads, 0, args);
+  return launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args);
 }
 
 // Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
@@ -480,7 +458,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   const size_t twb = align_up((size_t)c->N * cplx, 256);
   const size_t wb = align_up((size_t)c->plane * sizeof(float), 256);
   const size_t maskb = align_up((size_t)c->plane, 256);
-  const int max_blocks = std::max({row_geom(c, true).blocks, c->vec_blocks, cg_step_blocks(c->vec / 2)});
+  const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
   const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + partb + scb;
@@ -787,14 +765,14 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     if (e == cudaSuccess) e = q_adj_col(c, c->x);
     mark();
     a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum;
-    a.alpha = al; a.reduce = nlv::RED_PQ; a.part_early = 1;
+    a.alpha = al; a.reduce = nlv::RED_PQ;
     if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
     mark();
     a = base_args(c); a.reduce = nlv::RED_RR_UPDATE;
     const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
     float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
     void* args1[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
-    if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, cg_step_blocks(n2), kVecThreads, 0, args1);
+    if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args1);
     mark();
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
