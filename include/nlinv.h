@@ -130,6 +130,43 @@ NLINV_API nlinv_status nlinv_simulate(nlinv_ctx* ctx, const nlinv_c32* rho, cons
 NLINV_API nlinv_status nlinv_reconstruct(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x_ref,
                                nlinv_c32* x_inout, double* resid);
 
+/* ---------------------------------------------------------------------------------------------- batches ----
+ * Many independent frames (slices, series of different patients, ...) of uneven grid side and coil count,
+ * reconstructed together: every pass of Eq. 3 is one launch per grid side covering all frames of that side, and
+ * the sides run as parallel branches of one captured graph.  Each frame has its own workspace and its own CG and
+ * Newton scalars, so a frame's result is its single-frame reconstruction up to the summation order of the FP64
+ * scalars (the block partition of a batched pass differs from a single-frame pass). */
+typedef struct {
+  int n;                    /* grid side of the frame (see nlinv_supported_size); fov = n/4 */
+  int ncoils;               /* coils of the frame, 1..64 */
+  const nlinv_c32* y;       /* J planes of gridded data */
+  const uint8_t* mask;      /* sampling pattern */
+  const nlinv_c32* x_ref;   /* regularisation centre (1+J planes) or NULL for the start value */
+  nlinv_c32* x_inout;       /* start value in, result out (1+J planes) */
+  double* resid;            /* NULL or a HOST array of newton_steps+1 doubles (|y - F x_n|) */
+} nlinv_frame_desc;
+
+typedef struct nlinv_batch nlinv_batch;
+
+/* Creates a batch for nframes frames whose shapes are frames[i].n and frames[i].ncoils (the pointers are not used
+ * here).  params supplies the solver schedule and the Sobolev weight (its n, ncoils, fov and use_graph are
+ * ignored).  stream as for nlinv_create.  Allocates one workspace per frame and captures the whole batched
+ * reconstruction as one CUDA graph.  Errors: EINVAL, ENOMEM, ECUDA (message via nlinv_last_error(NULL)). */
+NLINV_API nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const nlinv_frame_desc* frames,
+                                          void* stream, nlinv_batch** out);
+
+/* Reconstructs all frames (Eq. 3 with the batch's schedule): frames must have the shapes given at creation, in
+ * the same order.  Pointers may be device or host memory as for nlinv_reconstruct.  Returns after queuing, unless
+ * a resid array is given or an x_inout is host memory (then it waits).  Errors: EINVAL, ECUDA, EBREAKDOWN (any
+ * frame, when the call waited). */
+NLINV_API nlinv_status nlinv_reconstruct_batch(nlinv_batch* batch, int nframes, const nlinv_frame_desc* frames);
+
+/* Kernel launches of one batched reconstruction (the graph's kernel nodes); -1 for NULL. */
+NLINV_API long nlinv_batch_launch_count(const nlinv_batch* batch);
+
+/* Waits for the batch's stream and frees it.  NULL is accepted. */
+NLINV_API nlinv_status nlinv_batch_destroy(nlinv_batch* batch);
+
 /* Waits up to timeout_s seconds (< 0: no limit) for the context's queued work.  ETIMEOUT if it is still running,
  * EBREAKDOWN if a CG breakdown was flagged since the last check (the flag is then cleared), ECUDA on a CUDA
  * error. */

@@ -25,6 +25,12 @@ class Params(C.Structure):
                 ("sobolev_a", _dbl), ("sobolev_l", _dbl), ("fov", _int), ("use_graph", _int)]
 
 
+class FrameDesc(C.Structure):
+    """Mirror of nlinv_frame_desc."""
+    _fields_ = [("n", _int), ("ncoils", _int), ("y", _vp), ("mask", _vp), ("x_ref", _vp), ("x_inout", _vp),
+                ("resid", C.POINTER(_dbl))]
+
+
 SIGNATURES = {
     "nlinv_supported_size": (_int, [_int]),
     "nlinv_default_params": (_int, [C.POINTER(Params), _int, _int]),
@@ -39,6 +45,10 @@ SIGNATURES = {
     "nlinv_wait": (_int, [_vp, _dbl]),
     "nlinv_profile_cg": (_int, [_vp, _int, C.POINTER(_dbl)]),
     "nlinv_forward_noalloc": (_int, [C.POINTER(Params), _vp, _vp, _vp, _vp]),
+    "nlinv_batch_create": (_int, [C.POINTER(Params), _int, C.POINTER(FrameDesc), _vp, C.POINTER(_vp)]),
+    "nlinv_reconstruct_batch": (_int, [_vp, _int, C.POINTER(FrameDesc)]),
+    "nlinv_batch_launch_count": (_long, [_vp]),
+    "nlinv_batch_destroy": (_int, [_vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
     "nlinv_last_error": (C.c_char_p, [_vp]),
 }

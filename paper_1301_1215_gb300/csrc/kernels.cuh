@@ -67,6 +67,8 @@ struct KArgs {
   Scalars* sc;
   int reduce;               // Reduce
   int slot;                 // RED_RESID index
+  const float2* q;          // CG step: A p
+  long n2;                  // vector passes: number of float4 (two complex values each)
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -140,21 +142,23 @@ __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slo
 
 // Every thread passes its FP32 partial; per-block sums in FP64 go to partials[], and the last block to finish
 // adds them in block order (so the result does not depend on scheduling) and updates the scalars.
-__device__ __forceinline__ void grid_reduce(float mine, const KArgs& A) {
+// bid / nblk: this block's index and the number of blocks working on the same problem (the whole grid, or one
+// frame's share of a batched grid).
+__device__ __forceinline__ void grid_reduce(float mine, const KArgs& A, int bid, int nblk) {
   __shared__ double red[32];
   __shared__ bool last;
   double s = block_sum((double)mine, red);
   if (threadIdx.x == 0) {
-    A.partials[blockIdx.x] = s;
+    A.partials[bid] = s;
     __threadfence();
     unsigned t = atomicAdd(&A.sc->ticket, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == (unsigned)nblk - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double acc = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) acc += __ldcg(&A.partials[i]);
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += __ldcg(&A.partials[i]);
   double total = block_sum(acc, red);
   if (threadIdx.x == 0) {
     finalize_scalar(A.sc, A.reduce, A.slot, total);
@@ -240,10 +244,10 @@ constexpr int kRowCtasPerSM = 2;
 // Omega (the channel summation of Table 1) plus the mode's alpha term.  Every block takes an equal slice of the
 // plane after its rows, all of its threads working on it; each thread issues its loads before its stores.
 template <int MODE>
-__device__ __forceinline__ float rho_slice(const KArgs& A) {
+__device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
   const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
   const long plane = (long)N * N;
-  const long e_begin = (long)blockIdx.x * A.rho_per_cta;
+  const long e_begin = (long)bid * A.rho_per_cta;
   const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
   const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
   float acc = 0.f;
@@ -295,12 +299,10 @@ __device__ __forceinline__ float rho_slice(const KArgs& A) {
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
 template <int N1, int N2, int MODE>
-__global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
+__device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
   constexpr int N = S::N, TL = S::TL, E = S::E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_enter();
   const int LANES = blockDim.x / TL;
   const int lane = threadIdx.x / TL, idx = threadIdx.x % TL;
   const int f = A.f, Wc = A.Wc;
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   const float2* twA = (const float2*)(smem_raw + L.tw);
   const float2* twB = twA + N;
   const float rs = rsqrtf((float)N);
-  const int r_begin = blockIdx.x * A.rows_per_cta;
+  const int r_begin = bid * A.rows_per_cta;
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
@@ -461,8 +463,15 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   __syncthreads();       // the next round restages the side rows
   }  // rounds
 
-  if constexpr (T::has_rho) acc += rho_slice<MODE>(A);
-  if constexpr (T::reduces) grid_reduce(acc, A);
+  if constexpr (T::has_rho) acc += rho_slice<MODE>(A, bid);
+  if constexpr (T::reduces) grid_reduce(acc, A, bid, nblk);
+}
+
+template <int N1, int N2, int MODE>
+__global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  row_pass_body<N1, N2, MODE>(A, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----
@@ -527,16 +536,14 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
 }
 
 template <int N1, int N2, int MODE>
-__global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
+__device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  pdl_enter();
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
   const int f = A.f, Wc = A.Wc;
   const int strips = (Wc + C - 1) / C;
-  const int j = blockIdx.x / strips;
-  const int cc0 = (blockIdx.x % strips) * C;
+  const int j = bid / strips;
+  const int cc0 = (bid % strips) * C;
   const int cc = cc0 + lane;
   const bool active = cc < Wc && j < A.nrows;
   const int x2 = to_natural(cc, N, f);
@@ -647,6 +654,60 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs 
   }
 }
 
+template <int N1, int N2, int MODE>
+__global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  col_pass_body<N1, N2, MODE>(A, blockIdx.x, smem_raw);
+}
+
+// --------------------------------------------------------------------------------------------- batches ----
+// A batched launch runs one pass for several independent frames of the same grid side: frame f owns the blocks
+// [first[f], first[f+1]) and its own arguments args[f] (pointers into its own workspace).  Each block finds its
+// frame, copies that frame's arguments into shared memory and runs the same pass body as a single-frame launch.
+struct BatchArgs {
+  const KArgs* args;       // per-frame arguments (device)
+  const int* first;        // nframes + 1 block offsets (device)
+  int nframes;
+};
+
+__device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int& bid, int& nblk) {
+  __shared__ KArgs sa;
+  __shared__ int sf, sb, sn;
+  if (threadIdx.x == 0) {
+    int f = 0;
+    while (f + 1 < B.nframes && B.first[f + 1] <= (int)blockIdx.x) ++f;
+    sf = f;
+    sb = (int)blockIdx.x - B.first[f];
+    sn = B.first[f + 1] - B.first[f];
+  }
+  __syncthreads();
+  const int* src = (const int*)(B.args + sf);
+  for (int i = threadIdx.x; i < (int)(sizeof(KArgs) / sizeof(int)); i += blockDim.x) ((int*)&sa)[i] = src[i];
+  bid = sb;
+  nblk = sn;
+  __syncthreads();
+  return sa;
+}
+
+template <int N1, int N2, int MODE>
+__global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass_batch(const BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  int bid, nblk;
+  const KArgs& A = batch_frame(B, bid, nblk);
+  row_pass_body<N1, N2, MODE>(A, bid, nblk, smem_raw);
+}
+
+template <int N1, int N2, int MODE>
+__global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass_batch(const BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  int bid, nblk;
+  const KArgs& A = batch_frame(B, bid, nblk);
+  col_pass_body<N1, N2, MODE>(A, bid, smem_raw);
+}
+
 // ------------------------------------------------------------------------------- per-size kernel table ----
 struct SizeKernels {
   int N1, N2;
@@ -656,6 +717,8 @@ struct SizeKernels {
   int sm_lane_col;          // the same for column passes (bank-conflict padding)
   const void* row[NUM_ROW_MODES];
   const void* col[NUM_COL_MODES];
+  const void* row_batch[NUM_ROW_MODES];
+  const void* col_batch[NUM_COL_MODES];
   size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
   size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane_col, Wc).total; }
 };
@@ -701,6 +764,19 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.col[COL_SIM_FFT] = (const void*)col_pass<N1, N2, COL_SIM_FFT>;
   s.col[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT>;
   s.col[COL_IFFT_ADJ_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_ADJ_FFT>;
+  s.row_batch[ROW_W_IFFT] = (const void*)row_pass_batch<N1, N2, ROW_W_IFFT>;
+  s.row_batch[ROW_PSF] = (const void*)row_pass_batch<N1, N2, ROW_PSF>;
+  s.row_batch[ROW_FFT_P_OUT] = (const void*)row_pass_batch<N1, N2, ROW_FFT_P_OUT>;
+  s.row_batch[ROW_FFT_RESID] = (const void*)row_pass_batch<N1, N2, ROW_FFT_RESID>;
+  s.row_batch[ROW_P_IFFT] = (const void*)row_pass_batch<N1, N2, ROW_P_IFFT>;
+  s.row_batch[ROW_FFT_W_ADJ] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_ADJ>;
+  s.row_batch[ROW_FFT_W_NORMAL] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_NORMAL>;
+  s.row_batch[ROW_FFT_W_RHS] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_RHS>;
+  s.col_batch[COL_IFFT_C] = (const void*)col_pass_batch<N1, N2, COL_IFFT_C>;
+  s.col_batch[COL_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_PROD_FFT>;
+  s.col_batch[COL_SIM_FFT] = (const void*)col_pass_batch<N1, N2, COL_SIM_FFT>;
+  s.col_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT>;
+  s.col_batch[COL_IFFT_ADJ_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_ADJ_FFT>;
   return s;
 }
 

@@ -32,13 +32,15 @@ namespace {
 thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
-// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE.   n2 = number of complex pairs (float4 accesses).
-__global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, const float4* __restrict__ q4,
-                               float4* __restrict__ r4, float4* __restrict__ dx4, long n2) {
-  nlv::pdl_enter();
+// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE, over this block's share of the A.n2 float4.
+__device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
   const float a = (float)A.sc->alpha;
+  const float4* __restrict__ p4 = (const float4*)A.p;
+  const float4* __restrict__ q4 = (const float4*)A.q;
+  float4* __restrict__ r4 = (float4*)A.r;
+  float4* __restrict__ dx4 = (float4*)A.dx;
   float acc = 0.f;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+  for (long i = bid * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)nblk * blockDim.x) {
     float4 p = p4[i], q = q4[i], r = r4[i], d = dx4[i];
     d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
     r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
@@ -46,17 +48,39 @@ __global__ void cg_step_kernel(const KArgs A, const float4* __restrict__ p4, con
     r4[i] = r;
     acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
   }
-  nlv::grid_reduce(acc, A);
+  nlv::grid_reduce(acc, A, bid, nblk);
 }
 
-// x += dx
-__global__ void add_kernel(const float4* __restrict__ d4, float4* __restrict__ x4, long n2) {
-  nlv::pdl_enter();
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n2; i += (long)gridDim.x * blockDim.x) {
+// x += dx (x = A.dst)
+__device__ __forceinline__ void add_body(const KArgs& A, int bid, int nblk) {
+  const float4* __restrict__ d4 = (const float4*)A.dx;
+  float4* __restrict__ x4 = (float4*)A.dst;
+  for (long i = bid * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)nblk * blockDim.x) {
     float4 d = d4[i], x = x4[i];
     x.x += d.x; x.y += d.y; x.z += d.z; x.w += d.w;
     x4[i] = x;
   }
+}
+
+__global__ void cg_step_kernel(const KArgs A) {
+  nlv::pdl_enter();
+  cg_step_body(A, blockIdx.x, gridDim.x);
+}
+__global__ void add_kernel(const KArgs A) {
+  nlv::pdl_enter();
+  add_body(A, blockIdx.x, gridDim.x);
+}
+__global__ void cg_step_batch(const nlv::BatchArgs B) {
+  nlv::pdl_enter();
+  int bid, nblk;
+  const KArgs& A = nlv::batch_frame(B, bid, nblk);
+  cg_step_body(A, bid, nblk);
+}
+__global__ void add_batch(const nlv::BatchArgs B) {
+  nlv::pdl_enter();
+  int bid, nblk;
+  const KArgs& A = nlv::batch_frame(B, bid, nblk);
+  add_body(A, bid, nblk);
 }
 
 constexpr int kVecThreads = 256;
@@ -94,6 +118,14 @@ struct nlinv_ctx {
   long graph_launches = 0;
   long launches = 0;
   bool have_state = false;    // a reconstruction has filled the workspace
+  int batch_lanes = 0;        // > 0: frame of a batch; row passes use this many lanes and one round per block
+  struct Rec {
+    const void* fn;
+    int grid, block;
+    size_t smem;
+    KArgs args;
+  };
+  std::vector<Rec>* rec = nullptr;   // non-null: launches are recorded instead of issued
   bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   std::string err;
@@ -139,6 +171,15 @@ KArgs base_args(const nlinv_ctx* c) {
 }
 
 nlv::RowGrid row_geom(const nlinv_ctx* c, bool with_rho) {
+  if (c->batch_lanes > 0) {           // batch frames: equal block shapes for every frame of a grid side
+    nlv::RowGrid g{};
+    const int rows = c->J * c->N;
+    g.lanes = std::min(c->batch_lanes, rows);
+    g.rows_per_cta = g.lanes;
+    g.blocks = (rows + g.lanes - 1) / g.lanes;
+    g.rho_per_cta = with_rho ? (int)((c->plane + g.blocks - 1) / g.blocks) : 0;
+    return g;
+  }
   return nlv::row_grid(c->k, c->J * c->N, with_rho ? c->plane : 0, c->sms, c->row_ctas_per_sm);
 }
 
@@ -151,6 +192,10 @@ int col_blocks(const nlinv_ctx* c) {
 // the current one drains (about 1% per frame on the 384 x 384, 10-coil series).
 cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
   c->launches++;
+  if (c->rec) {                       // every pass takes one KArgs
+    c->rec->push_back({fn, grid, block, smem, *(const KArgs*)args[0]});
+    return cudaSuccess;
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -229,6 +274,29 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
+// dx += alpha p, r -= alpha q, |r|^2 -> beta
+cudaError_t q_cg_step(nlinv_ctx* c) {
+  KArgs a = base_args(c);
+  a.reduce = nlv::RED_RR_UPDATE;
+  a.p = c->p;
+  a.q = c->q;
+  a.r = c->r;
+  a.dx = c->dx;
+  a.n2 = c->vec / 2;
+  void* args[] = {&a};
+  return launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args);
+}
+
+// x += dx
+cudaError_t q_add(nlinv_ctx* c) {
+  KArgs a = base_args(c);
+  a.dx = c->dx;
+  a.dst = c->x;
+  a.n2 = c->vec / 2;
+  void* args[] = {&a};
+  return launch(c, (const void*)add_kernel, c->vec_blocks, kVecThreads, 0, args);
+}
+
 // One CG iteration on (DF^H DF + alpha) for linearisation point x.  The direction update p = r + beta p of the
 // previous iteration is folded into the passes that first read p (beta = 0 right after the right-hand side).
 //   K1 row  p_c = r_c + beta p_c; T = W^-1 p_c (first axis)
@@ -268,13 +336,7 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   a.alpha = alpha;
   a.reduce = nlv::RED_PQ;
   if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
-  a = base_args(c);
-  a.reduce = nlv::RED_RR_UPDATE;
-  const long n2 = c->vec / 2;
-  const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
-  float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
-  void* args[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
-  return launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args);
+  return q_cg_step(c);
 }
 
 // Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
@@ -320,11 +382,7 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
     for (int i = 0; i < P.cg_iters; ++i)
       if ((e = q_cg_iter(c, c->x, al)) != cudaSuccess) return e;
-    const long n2 = c->vec / 2;
-    const float4* d4 = (const float4*)c->dx;
-    float4* x4 = (float4*)c->x;
-    void* args[] = {&d4, &x4, (void*)&n2};
-    if ((e = launch(c, (const void*)add_kernel, c->vec_blocks, kVecThreads, 0, args)) != cudaSuccess) return e;
+    if ((e = q_add(c)) != cudaSuccess) return e;
     c->last_alpha = alpha;
     alpha = std::max(alpha * P.alpha_q, P.alpha_min);
   }
@@ -390,7 +448,12 @@ nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils) {
   return NLINV_OK;
 }
 
-nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** out) {
+}  // extern "C"
+
+namespace {
+
+// Context set-up shared by nlinv_create and the frames of a batch (batch_lanes > 0: fixed row-pass block shape).
+nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lanes, nlinv_ctx** out) {
   nlinv_ctx* c = nullptr;
   if (!out) return fail(nullptr, NLINV_EINVAL, "out is NULL");
   *out = nullptr;
@@ -406,6 +469,7 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   c->plane = (long)c->N * c->N;
   c->vec = (long)(1 + c->J) * c->plane;
   c->k = nlv::find_size(c->N);
+  c->batch_lanes = batch_lanes;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { g_create_error = std::string("cudaGetDevice: ") + cudaGetErrorString(e); delete c; return NLINV_ECUDA; }
   if (stream) {
@@ -420,6 +484,8 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "0") != 0;
   c->sms = std::max(1, sms);
   c->vec_blocks = c->sms * 4;
+  if (batch_lanes > 0)   // a frame of a batch: vector passes get blocks in proportion to its size
+    c->vec_blocks = (int)std::min<long>(c->vec_blocks, std::max<long>(1, c->vec / 2 / (kVecThreads * 8)));
 
   // dynamic shared memory above the 48 KB default, within the device's opt-in limit
   int smem_optin = 0;
@@ -439,9 +505,14 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
       smem_err = "cudaFuncSetAttribute failed";
   };
   const int lanes_max = std::max(row_geom(c, false).lanes, row_geom(c, true).lanes);
-  for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m)
+  for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) {
     allow(c->k->row[m], c->k->row_smem(m, lanes_max));
-  for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) allow(c->k->col[m], c->k->col_smem(m, c->Wc));
+    if (smem_err.empty()) allow(c->k->row_batch[m], c->k->row_smem(m, lanes_max));
+  }
+  for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) {
+    allow(c->k->col[m], c->k->col_smem(m, c->Wc));
+    if (smem_err.empty()) allow(c->k->col_batch[m], c->k->col_smem(m, c->Wc));
+  }
   if (!smem_err.empty()) {
     cudaGetLastError();
     g_create_error = smem_err;
@@ -524,6 +595,14 @@ nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** 
   }
   *out = c;
   return NLINV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** out) {
+  return create_ctx(params, stream, 0, out);
 }
 
 nlinv_status nlinv_destroy(nlinv_ctx* c) {
@@ -745,7 +824,6 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   for (int i = 0; i <= K; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
   double acc[K] = {0};
   const float al = (float)c->last_alpha;
-  const long n2 = c->vec / 2;
   cudaError_t e = cudaSuccess;
   for (int it = 0; it < reps && e == cudaSuccess; ++it) {
     int k = 0;
@@ -768,11 +846,7 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     a.alpha = al; a.reduce = nlv::RED_PQ;
     if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
     mark();
-    a = base_args(c); a.reduce = nlv::RED_RR_UPDATE;
-    const float4 *p4 = (const float4*)c->p, *q4 = (const float4*)c->q;
-    float4 *r4 = (float4*)c->r, *d4 = (float4*)c->dx;
-    void* args1[] = {&a, &p4, &q4, &r4, &d4, (void*)&n2};
-    if (e == cudaSuccess) e = launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args1);
+    if (e == cudaSuccess) e = q_cg_step(c);
     mark();
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
@@ -788,6 +862,263 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
 }
 
 long nlinv_last_launch_count(const nlinv_ctx* c) { return c ? c->launches : -1; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------- batches ----
+struct nlinv_batch {
+  nlinv_params prm{};
+  std::vector<nlinv_ctx*> frames;           // per-frame workspaces (they never launch by themselves)
+  std::vector<std::vector<int>> groups;     // frame indices per grid side
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<cudaStream_t> gstream;        // branch stream per group (group 0 runs on `stream`)
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  void* tables = nullptr;                   // device: per-launch frame arguments and block offsets
+  struct Launch {
+    int group;
+    const void* fn;
+    int grid, block;
+    size_t smem;
+    nlv::BatchArgs args;
+  };
+  std::vector<Launch> launches;
+  cudaGraphExec_t graph = nullptr;
+  bool pdl = true;
+};
+
+namespace {
+
+void batch_free(nlinv_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (size_t g = 1; g < b->gstream.size(); ++g)
+    if (b->gstream[g]) cudaStreamDestroy(b->gstream[g]);
+  for (cudaEvent_t e : b->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->tables) cudaFree(b->tables);
+  for (nlinv_ctx* c : b->frames) nlinv_destroy(c);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// The batched kernel that runs the single-frame pass fn for several frames.
+const void* batched_kernel(const SizeKernels* k, const void* fn) {
+  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m)
+    if (fn == k->row[m]) return k->row_batch[m];
+  for (int m = 0; m < nlv::NUM_COL_MODES; ++m)
+    if (fn == k->col[m]) return k->col_batch[m];
+  if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
+  if (fn == (const void*)add_kernel) return (const void*)add_batch;
+  return nullptr;
+}
+
+nlinv_status batch_fail(nlinv_batch* b, nlinv_status st, const std::string& msg) {
+  g_create_error = msg;
+  batch_free(b);
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const nlinv_frame_desc* frames,
+                                void* stream, nlinv_batch** out) {
+  if (!out) return fail(nullptr, NLINV_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!params || !frames || nframes < 1 || nframes > 4096)
+    return fail(nullptr, NLINV_EINVAL, "params, frames and 1 <= nframes <= 4096 are required");
+  nlinv_batch* b = new (std::nothrow) nlinv_batch();
+  if (!b) return fail(nullptr, NLINV_ENOMEM, "host allocation failed");
+  b->prm = *params;
+  if (const char* v = std::getenv("NLINV_PDL")) b->pdl = std::strcmp(v, "0") != 0;
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return batch_fail(b, NLINV_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+    b->own_stream = true;
+  }
+  // one workspace per frame, grouped by grid side
+  std::vector<int> sides;
+  for (int i = 0; i < nframes; ++i) {
+    nlinv_params fp = *params;
+    fp.n = frames[i].n;
+    fp.ncoils = frames[i].ncoils;
+    fp.fov = frames[i].n / 4;
+    fp.use_graph = 0;
+    const SizeKernels* k = nlv::find_size(fp.n);
+    if (!k) return batch_fail(b, NLINV_EINVAL, "frame " + std::to_string(i) + ": unsupported grid side");
+    nlinv_ctx* c = nullptr;
+    const nlinv_status st = create_ctx(&fp, b->stream, nlv::kRowMaxThreads / k->tl, &c);
+    if (st != NLINV_OK) return batch_fail(b, st, "frame " + std::to_string(i) + ": " + g_create_error);
+    b->frames.push_back(c);
+    size_t g = 0;
+    while (g < sides.size() && sides[g] != fp.n) ++g;
+    if (g == sides.size()) {
+      sides.push_back(fp.n);
+      b->groups.emplace_back();
+    }
+    b->groups[g].push_back(i);
+  }
+  // the launch sequence of every frame, merged launch by launch within each group
+  std::vector<std::vector<nlinv_ctx::Rec>> recs(nframes);
+  for (int i = 0; i < nframes; ++i) {
+    nlinv_ctx* c = b->frames[i];
+    c->rec = &recs[i];
+    e = q_reconstruct(c);
+    c->rec = nullptr;
+    if (e != cudaSuccess) return batch_fail(b, NLINV_ECUDA, std::string("recording: ") + cudaGetErrorString(e));
+  }
+  std::vector<char> host;
+  std::vector<size_t> arg_off, first_off;
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    const std::vector<int>& fr = b->groups[g];
+    const size_t L = recs[fr[0]].size();
+    const SizeKernels* k = b->frames[fr[0]]->k;
+    for (int i : fr)
+      if (recs[i].size() != L) return batch_fail(b, NLINV_EINVAL, "frames of one grid side differ in schedule");
+    for (size_t l = 0; l < L; ++l) {
+      nlinv_batch::Launch bl{};
+      bl.group = (int)g;
+      bl.fn = batched_kernel(k, recs[fr[0]][l].fn);
+      bl.block = recs[fr[0]][l].block;
+      if (!bl.fn) return batch_fail(b, NLINV_EINVAL, "internal: no batched form of a pass");
+      size_t off = (host.size() + 15) / 16 * 16;
+      host.resize(off + fr.size() * sizeof(KArgs));
+      arg_off.push_back(off);
+      std::vector<int> first(fr.size() + 1, 0);
+      for (size_t t = 0; t < fr.size(); ++t) {
+        const nlinv_ctx::Rec& r = recs[fr[t]][l];
+        if (r.fn != recs[fr[0]][l].fn || r.block != bl.block)
+          return batch_fail(b, NLINV_EINVAL, "frames of one grid side differ in pass shapes");
+        std::memcpy(host.data() + off + t * sizeof(KArgs), &r.args, sizeof(KArgs));
+        first[t + 1] = first[t] + r.grid;
+        bl.smem = std::max(bl.smem, r.smem);
+      }
+      bl.grid = first.back();
+      off = (host.size() + 15) / 16 * 16;
+      host.resize(off + first.size() * sizeof(int));
+      std::memcpy(host.data() + off, first.data(), first.size() * sizeof(int));
+      first_off.push_back(off);
+      bl.args.nframes = (int)fr.size();
+      b->launches.push_back(bl);
+    }
+  }
+  e = cudaMalloc(&b->tables, host.size());
+  if (e != cudaSuccess) { cudaGetLastError(); return batch_fail(b, NLINV_ENOMEM, "batch tables: cudaMalloc failed"); }
+  e = cudaMemcpy(b->tables, host.data(), host.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return batch_fail(b, NLINV_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e));
+  for (size_t l = 0; l < b->launches.size(); ++l) {
+    b->launches[l].args.args = (const KArgs*)((char*)b->tables + arg_off[l]);
+    b->launches[l].args.first = (const int*)((char*)b->tables + first_off[l]);
+  }
+  // one graph: the groups as parallel branches
+  const size_t G = b->groups.size();
+  b->gstream.assign(G, nullptr);
+  b->ev_join.assign(G, nullptr);
+  b->gstream[0] = b->stream;
+  for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
+    e = cudaStreamCreateWithFlags(&b->gstream[g], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[g], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return batch_fail(b, NLINV_ECUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
+  for (size_t g = 1; g < G && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->gstream[g], b->ev_fork, 0);
+  for (size_t l = 0; l < b->launches.size() && e == cudaSuccess; ++l) {
+    nlinv_batch::Launch& bl = b->launches[l];
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(bl.grid);
+    cfg.blockDim = dim3(bl.block);
+    cfg.dynamicSmemBytes = bl.smem;
+    cfg.stream = b->gstream[bl.group];
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = b->pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void* args[] = {&bl.args};
+    e = cudaLaunchKernelExC(&cfg, bl.fn, args);
+  }
+  for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
+    e = cudaEventRecord(b->ev_join[g], b->gstream[g]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[g], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return batch_fail(b, NLINV_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  *out = b;
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_reconstruct_batch(nlinv_batch* b, int nframes, const nlinv_frame_desc* frames) {
+  if (!b) return NLINV_EINVAL;
+  if (!frames || nframes != (int)b->frames.size())
+    return fail(nullptr, NLINV_EINVAL, "nframes and the frames must match the batch");
+  bool wait = false;
+  for (int i = 0; i < nframes; ++i) {
+    nlinv_ctx* c = b->frames[i];
+    const nlinv_frame_desc& d = frames[i];
+    if (d.n != c->N || d.ncoils != c->J) return fail(nullptr, NLINV_EINVAL, "frame " + std::to_string(i) + ": shape differs");
+    if (!d.y || !d.mask || !d.x_inout) return fail(nullptr, NLINV_EINVAL, "frame " + std::to_string(i) + ": NULL buffer");
+    wait = wait || d.resid || !is_device_ptr(d.x_inout);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < nframes && e == cudaSuccess; ++i) {
+    nlinv_ctx* c = b->frames[i];
+    const nlinv_frame_desc& d = frames[i];
+    const size_t vb = c->vec * sizeof(float2), db = (size_t)c->J * c->plane * sizeof(float2);
+    e = cudaMemcpyAsync(c->y, d.y, db, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->mask, d.mask, (size_t)c->plane, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->x, d.x_inout, vb, cudaMemcpyDefault, b->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->xref, d.x_ref ? (const void*)d.x_ref : (const void*)c->x, vb, cudaMemcpyDefault, b->stream);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+  for (int i = 0; i < nframes && e == cudaSuccess; ++i) {
+    nlinv_ctx* c = b->frames[i];
+    e = cudaMemcpyAsync(frames[i].x_inout, c->x, c->vec * sizeof(float2), cudaMemcpyDefault, b->stream);
+  }
+  if (e != cudaSuccess) return fail(nullptr, NLINV_ECUDA, std::string("nlinv_reconstruct_batch: ") + cudaGetErrorString(e));
+  if (!wait) return NLINV_OK;
+  std::vector<Scalars> hs(nframes);
+  for (int i = 0; i < nframes && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(&hs[i], b->frames[i]->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return fail(nullptr, NLINV_ECUDA, std::string("nlinv_reconstruct_batch: ") + cudaGetErrorString(e));
+  bool broke = false;
+  for (int i = 0; i < nframes; ++i) {
+    if (frames[i].resid)
+      for (int n = 0; n <= b->prm.newton_steps; ++n) frames[i].resid[n] = hs[i].resid[n];
+    if (hs[i].flags & 1) {
+      broke = true;
+      int zero = 0;
+      cudaMemcpy(&b->frames[i]->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+  }
+  if (broke) return fail(nullptr, NLINV_EBREAKDOWN, "CG breakdown in at least one frame");
+  return NLINV_OK;
+}
+
+long nlinv_batch_launch_count(const nlinv_batch* b) { return b ? (long)b->launches.size() : -1; }
+
+nlinv_status nlinv_batch_destroy(nlinv_batch* b) {
+  batch_free(b);
+  return NLINV_OK;
+}
 
 const char* nlinv_last_error(const nlinv_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 

@@ -17,7 +17,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["Nlinv", "supported_size", "NlinvError"]
+__all__ = ["Nlinv", "NlinvBatch", "supported_size", "NlinvError"]
 
 NlinvError = _lib.NlinvError
 
@@ -212,3 +212,94 @@ class Nlinv:
     def last_launch_count(self) -> int:
         """Kernel launches queued by the last call (kernel nodes of the graph when one was replayed)."""
         return int(self._lib.nlinv_last_launch_count(self._h))
+
+
+class NlinvBatch:
+    """Independent frames of uneven grid side and coil count reconstructed together (nlinv_reconstruct_batch):
+    every pass is one launch per grid side over all frames of that side, the sides run as parallel graph branches.
+
+    ``shapes`` lists (n, ncoils) per frame; the solver options are those of :class:`Nlinv` (fov = n/4)."""
+
+    def __init__(self, shapes, *, newton_steps: int = 7, cg_iters: int = 30, alpha0: float = 1.0,
+                 alpha_q: float = 0.5, alpha_min: float = 0.0, sobolev_a: float = 220.0, sobolev_l: float = 32.0,
+                 device=None):
+        lib = _lib.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("NlinvBatch needs a CUDA device; there is no CPU implementation")
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.shapes = [(int(n), int(j)) for n, j in shapes]
+        p = _lib.Params()
+        lib.nlinv_default_params(C.byref(p), self.shapes[0][0], self.shapes[0][1])
+        p.newton_steps, p.cg_iters = int(newton_steps), int(cg_iters)
+        p.alpha0, p.alpha_q, p.alpha_min = float(alpha0), float(alpha_q), float(alpha_min)
+        p.sobolev_a, p.sobolev_l = float(sobolev_a), float(sobolev_l)
+        self.params = p
+        descs = (_lib.FrameDesc * len(self.shapes))()
+        for d, (n, j) in zip(descs, self.shapes):
+            d.n, d.ncoils = n, j
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.Stream(self.device)
+            _lib.check(lib.nlinv_batch_create(C.byref(p), len(self.shapes), descs,
+                                              C.c_void_p(self.stream.cuda_stream), C.byref(self._h)), None)
+        self._lib = lib
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.nlinv_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.nlinv_batch_launch_count(self._h))
+
+    def reconstruct(self, ys, masks, xs=None, x_refs=None, resid: bool = False):
+        """Reconstructs every frame.  ``xs`` (start values, overwritten with the results; default rho = 1,
+        chat = 0) and ``x_refs`` are lists of (1+J, n, n) complex64 tensors; ``ys`` (J, n, n), ``masks`` (n, n)
+        uint8.  Tensors may live on the device or on the host.  Returns the list of results (and the residual
+        norms per frame when ``resid``)."""
+        nf = len(self.shapes)
+        if len(ys) != nf or len(masks) != nf:
+            raise ValueError("one y and one mask per frame are required")
+        if xs is None:
+            xs = []
+            for n, j in self.shapes:
+                x = torch.zeros((1 + j, n, n), dtype=torch.complex64, device=self.device)
+                x[0] = 1.0
+                xs.append(x)
+        descs = (_lib.FrameDesc * nf)()
+        bufs = [(C.c_double * (self.params.newton_steps + 1))() for _ in range(nf)] if resid else None
+        keep = []
+        for i, (n, j) in enumerate(self.shapes):
+            y, m, x = ys[i].contiguous(), masks[i].contiguous(), xs[i]
+            if tuple(y.shape) != (j, n, n) or tuple(m.shape) != (n, n) or tuple(x.shape) != (1 + j, n, n):
+                raise ValueError(f"frame {i}: shapes do not match ({n}, {j})")
+            if not x.is_contiguous() or x.dtype != torch.complex64 or y.dtype != torch.complex64 or m.dtype != torch.uint8:
+                raise TypeError(f"frame {i}: complex64 y/x (contiguous x) and uint8 mask are required")
+            xr = None if x_refs is None or x_refs[i] is None else x_refs[i].contiguous()
+            keep += [y, m, xr]
+            d = descs[i]
+            d.n, d.ncoils = n, j
+            d.y, d.mask, d.x_inout = y.data_ptr(), m.data_ptr(), x.data_ptr()
+            d.x_ref = None if xr is None else xr.data_ptr()
+            d.resid = C.cast(bufs[i], C.POINTER(C.c_double)) if resid else None
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        _lib.check(self._lib.nlinv_reconstruct_batch(self._h, nf, descs), None)
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        if resid:
+            return xs, [[float(v) for v in b] for b in bufs]
+        return xs
