@@ -151,6 +151,23 @@ def build_series(torch, ctx, W, frames, dev):
     return ys, masks
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over the ranks of the default process group (the value itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(steps_per_rank: int, world: int, slowest_ms: float) -> float:
+    """Whole-job frames/s of `world` independent replicas that each reconstructed steps_per_rank frames, the
+    slowest taking slowest_ms (replicas only: the frames of different ranks never exchange data)."""
+    return world * steps_per_rank / (slowest_ms / 1e3)
+
+
 def cg_bytes(n: int, J: int, fov: int):
     """Algorithmic bytes per launch of the kernels of one CG iteration: every input read once and every output
     written once (U = one complex64 plane, compact Omega columns Wc = 2 fov)."""
@@ -212,11 +229,8 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     frame_ms = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
     total_ms = sum(frame_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = replica_throughput(K, world, total_ms)
     p50 = frame_ms[len(frame_ms) // 2]
     p99 = frame_ms[min(len(frame_ms) - 1, int(round(0.99 * (len(frame_ms) - 1))))]
     finite = bool(torch.isfinite(torch.view_as_real(x)).all().item())

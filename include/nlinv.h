@@ -109,6 +109,11 @@ NLINV_API nlinv_status nlinv_adjoint(nlinv_ctx* ctx, const nlinv_c32* x, const u
 NLINV_API nlinv_status nlinv_normal(nlinv_ctx* ctx, const nlinv_c32* x, const uint8_t* mask, const nlinv_c32* d,
                           double alpha, nlinv_c32* out);
 
+/* Display image of an estimate x (1+J planes): rho * sqrt(sum_j |c_j|^2) on Omega, the customary coil-combined
+ * NLINV output (the paper does not describe its post-processing).  image_out: (2 fov) x (2 fov) complex values,
+ * row-major and centred (row i, column k hold the signed coordinates i - fov, k - fov). */
+NLINV_API nlinv_status nlinv_image(nlinv_ctx* ctx, const nlinv_c32* x, nlinv_c32* image_out);
+
 /* Gridded data of the signal equation (Eq. 1) for image-domain coil maps: y_out_j = P FFT(M rho coil_img_j).
  * rho: one plane; coil_img: J planes; y_out: J planes.  Used to synthesise test and benchmark data. */
 NLINV_API nlinv_status nlinv_simulate(nlinv_ctx* ctx, const nlinv_c32* rho, const nlinv_c32* coil_img, const uint8_t* mask,

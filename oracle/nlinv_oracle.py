@@ -138,6 +138,16 @@ def simulate(s: Setup, mask: np.ndarray, rho: np.ndarray, coil_img: np.ndarray) 
     return mask * fft2u(M * rho * coil_img)
 
 
+def image(s: Setup, x: np.ndarray) -> np.ndarray:
+    """Coil-combined image rho * sqrt(sum_j |c_j|^2) on Omega, centred (row i holds the signed coordinate i - fov):
+    the customary NLINV output, which removes the rho -> s rho, c -> c / s ambiguity up to a phase.  The paper does
+    not describe its post-processing; this is a reading."""
+    full = x[0] * np.sqrt(np.sum(np.abs(coils(s, x)) ** 2, axis=0))
+    shifted = np.fft.fftshift(full)
+    h = s.n // 2
+    return shifted[h - s.fov: h + s.fov, h - s.fov: h + s.fov]
+
+
 # ---------------------------------------------------------------------------------------------------------------
 # Conjugate gradients and the iteratively regularised Gauss-Newton method (Eq. 3)
 # ---------------------------------------------------------------------------------------------------------------

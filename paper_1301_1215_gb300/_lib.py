@@ -41,6 +41,7 @@ SIGNATURES = {
     "nlinv_adjoint": (_int, [_vp, _vp, _vp, _vp, _vp]),
     "nlinv_normal": (_int, [_vp, _vp, _vp, _vp, _dbl, _vp]),
     "nlinv_simulate": (_int, [_vp, _vp, _vp, _vp, _vp]),
+    "nlinv_image": (_int, [_vp, _vp, _vp]),
     "nlinv_reconstruct": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "nlinv_wait": (_int, [_vp, _dbl]),
     "nlinv_profile_cg": (_int, [_vp, _int, C.POINTER(_dbl)]),

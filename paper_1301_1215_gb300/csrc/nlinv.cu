@@ -62,6 +62,23 @@ __device__ __forceinline__ void add_body(const KArgs& A, int bid, int nblk) {
   }
 }
 
+// Display image rho * sqrt(sum_j |c_j|^2) on Omega, centred: out[i][k] for the signed coordinates (i - f, k - f).
+__global__ void image_kernel(const KArgs A) {
+  const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
+  const long total = (long)Wc * Wc;
+  for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < total; o += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(o / Wc), k = (int)(o % Wc);
+    const int cr = (i + f) % Wc, cc = (k + f) % Wc;           // compact indices of the signed coordinates
+    float s = 0.f;
+    for (int j = 0; j < J; ++j) {
+      const float2 c = A.coil[((size_t)j * Wc + cr) * Wc + cc];
+      s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
+    }
+    const float2 r = A.rho[(size_t)nlv::to_natural(cr, N, f) * N + nlv::to_natural(cc, N, f)];
+    A.dst[o] = nlv::cscale(r, sqrtf(s));
+  }
+}
+
 __global__ void cg_step_kernel(const KArgs A) {
   nlv::pdl_enter();
   cg_step_body(A, blockIdx.x, gridDim.x);
@@ -711,6 +728,23 @@ nlinv_status nlinv_normal(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask,
     e = row(c, nlv::ROW_FFT_W_NORMAL, a);
   }
   return finish_call(c, e, "nlinv_normal");
+}
+
+nlinv_status nlinv_image(nlinv_ctx* c, const nlinv_c32* x, nlinv_c32* image_out) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, x, "x")) || (s = check_dev(c, image_out, "image_out"))) return s;
+  c->launches = 0;
+  cudaError_t e = q_coils(c, (const float2*)x);
+  if (e == cudaSuccess) {
+    KArgs a = base_args(c);
+    a.rho = (const float2*)x;
+    a.coil = c->coil;
+    a.dst = (float2*)image_out;
+    void* args[] = {&a};
+    e = launch(c, (const void*)image_kernel, c->vec_blocks, kVecThreads, 0, args);
+  }
+  return finish_call(c, e, "nlinv_image");
 }
 
 nlinv_status nlinv_simulate(nlinv_ctx* c, const nlinv_c32* rho, const nlinv_c32* coil_img, const uint8_t* mask,

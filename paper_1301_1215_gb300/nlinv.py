@@ -152,6 +152,17 @@ class Nlinv:
         self._end()
         return out
 
+    def image(self, x, out=None) -> torch.Tensor:
+        """Display image rho * sqrt(sum_j |c_j|^2) on Omega, centred; shape (2 fov, 2 fov)."""
+        x = self._x(x)
+        w = 2 * self.params.fov
+        out = torch.empty((w, w), dtype=torch.complex64, device=self.device) if out is None else \
+            self._dev(out, (w, w), torch.complex64, "out")
+        self._begin()
+        self._check(self._lib.nlinv_image(self._h, _ptr(x), _ptr(out)))
+        self._end()
+        return out
+
     def simulate(self, rho, coil_img, mask, out=None) -> torch.Tensor:
         """Gridded signal-equation data (Eq. 1) for image-domain coils: P FFT(M rho c_j); shape (J, n, n)."""
         rho = self._dev(rho, (self.n, self.n), torch.complex64, "rho")

@@ -135,3 +135,13 @@ def test_host_pointer_rejected_by_operators(torch_cuda):
                                     C.c_void_p(y.data_ptr()))
         assert st == _lib.EINVAL
         assert b"device pointer" in ctx._lib.nlinv_last_error(ctx._h)
+
+
+@pytest.mark.parametrize("n,J,fov", [(64, 4, 13), (384, 10, 96)])
+def test_image_matches_oracle(torch_cuda, n, J, fov):
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    s, x, d, r, mask = _inputs(n, J, fov, seed=99)
+    with Nlinv(n, J, fov=fov) as ctx:
+        got = ctx.image(_t(torch, x)).cpu().numpy()
+    assert rel(got, O.image(s, x)) < TOL

@@ -357,3 +357,21 @@ def test_operator_breakdown_matches_table1(monkeypatch):
     one = measure(lambda: O.cg(lambda v: diag * v, b, 1))
     two = measure(lambda: O.cg(lambda v: diag * v, b, 2))
     assert two["dot"] - one["dot"] == t1["CG"]["scalar_product"] and two["fft"] == t1["CG"]["fft"]
+
+
+def test_image_of_flat_coils_is_centred_rho():
+    # a = 0 and chat = n delta_0 / sqrt(J) per coil give |c_j| = 1/sqrt(J), so sqrt(sum |c_j|^2) = 1
+    n, J, fov = 32, 2, 8
+    s = O.Setup(n, J, fov, a=0.0)
+    x = np.zeros((1 + J, n, n), complex)
+    x[0] = synth.random_complex((n, n), synth.rng_for(91))
+    x[1:, 0, 0] = n / np.sqrt(J)
+    img = O.image(s, x)
+    assert img.shape == (2 * fov, 2 * fov)
+    ref = np.fft.fftshift(x[0])[n // 2 - fov: n // 2 + fov, n // 2 - fov: n // 2 + fov]
+    assert rel(img, ref) < 1e-13
+    # invariance: rho -> 2 rho, chat -> chat / 2 leaves the image unchanged
+    y = x.copy()
+    y[0] *= 2.0
+    y[1:] /= 2.0
+    assert rel(O.image(s, y), img) < 1e-13
