@@ -64,6 +64,7 @@ __device__ __forceinline__ void add_body(const KArgs& A, int bid, int nblk) {
 
 // Display image rho * sqrt(sum_j |c_j|^2) on Omega, centred: out[i][k] for the signed coordinates (i - f, k - f).
 __global__ void image_kernel(const KArgs A) {
+  nlv::pdl_enter();
   const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
   const long total = (long)Wc * Wc;
   for (long o = blockIdx.x * (long)blockDim.x + threadIdx.x; o < total; o += (long)gridDim.x * blockDim.x) {
@@ -206,7 +207,8 @@ int col_blocks(const nlinv_ctx* c) {
 }
 
 // Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh): the next pass is scheduled while
-// the current one drains (about 1% per frame on the 384 x 384, 10-coil series).
+// the current one drains (about 1% per frame on the 384 x 384, 10-coil series).  Every kernel launched here must
+// call nlv::pdl_enter() before its first global memory access.
 cudaError_t launch(nlinv_ctx* c, const void* fn, int grid, int block, size_t smem, void** args) {
   c->launches++;
   if (c->rec) {                       // every pass takes one KArgs

@@ -97,3 +97,17 @@ def test_binding_refuses_without_gpu():
     from paper_1301_1215_gb300.nlinv import Nlinv
     with pytest.raises(RuntimeError):
         Nlinv(64, 4)
+
+
+def test_every_kernel_waits_for_its_predecessor():
+    # Passes are launched with programmatic stream serialisation, so each kernel must execute
+    # griddepcontrol.wait (nlv::pdl_enter) before touching global memory written by the pass before it.
+    csrc = os.path.join(ROOT, "paper_1301_1215_gb300", "csrc")
+    for name in os.listdir(csrc):
+        if not name.endswith((".cu", ".cuh")):
+            continue
+        lines = open(os.path.join(csrc, name)).read().splitlines()
+        for i, line in enumerate(lines):
+            if "__global__" in line and "(" in line and line.rstrip().endswith("{"):
+                body = "\n".join(lines[i + 1: i + 5])
+                assert "pdl_enter()" in body, f"{name}:{i + 1} kernel does not start with pdl_enter()"
