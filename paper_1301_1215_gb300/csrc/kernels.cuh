@@ -69,6 +69,11 @@ struct KArgs {
   int slot;                 // RED_RESID index
   const float2* q;          // CG step: A p
   long n2;                  // vector passes: number of float4 (two complex values each)
+  // Re<p, A p> without a last-block tail: the normal-operator pass only writes one FP64 partial per block into
+  // pq_part (pq_only = 1); the CG step, its one consumer, adds the n_pq partials itself to form alpha.
+  double* pq_part;
+  int n_pq;
+  int pq_only;
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -464,7 +469,15 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   }  // rounds
 
   if constexpr (T::has_rho) acc += rho_slice<MODE>(A, bid);
-  if constexpr (T::reduces) grid_reduce(acc, A, bid, nblk);
+  if constexpr (T::reduces) {
+    if (MODE == ROW_FFT_W_NORMAL && A.pq_only) {
+      __shared__ double red[32];
+      const double sblk = block_sum((double)acc, red);
+      if (threadIdx.x == 0) A.pq_part[bid] = sblk;
+    } else {
+      grid_reduce(acc, A, bid, nblk);
+    }
+  }
 }
 
 template <int N1, int N2, int MODE>

@@ -34,19 +34,49 @@ thread_local std::string g_create_error;
 // ------------------------------------------------------------------------------------------ vector kernels ----
 // dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE, over this block's share of the A.n2 float4.
 __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
-  const float a = (float)A.sc->alpha;
   const float4* __restrict__ p4 = (const float4*)A.p;
   const float4* __restrict__ q4 = (const float4*)A.q;
   float4* __restrict__ r4 = (float4*)A.r;
   float4* __restrict__ dx4 = (float4*)A.dx;
+  // first group of operands loaded while warp 0 forms alpha = |r|^2 / Re<p, A p> from the partials of the
+  // normal-operator pass (same order in every block; empty step at the rounding floor, flag on non-finite values)
+  const long stride = (long)nblk * blockDim.x;
+  long i = bid * (long)blockDim.x + threadIdx.x;
+  float4 p, q, r, d;
+  if (i < A.n2) { p = p4[i]; q = q4[i]; r = r4[i]; d = dx4[i]; }
+  __shared__ float s_alpha;
+  if (A.pq_part) {
+    if (threadIdx.x < 32) {
+      double t = 0.0;
+      for (int k = threadIdx.x; k < A.n_pq; k += 32) t += A.pq_part[k];
+      t = nlv::warp_sum(t);
+      if (threadIdx.x == 0) {
+        const double rr = A.sc->rr;
+        double a = 0.0;
+        if (!isfinite(t) || !isfinite(rr)) {
+          if (bid == 0) A.sc->flags |= 1;
+        } else if (rr != 0.0 && t > 0.0) {
+          a = rr / t;
+        }
+        if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; }
+        s_alpha = (float)a;
+      }
+    }
+    __syncthreads();
+  } else if (threadIdx.x == 0) {
+    s_alpha = (float)A.sc->alpha;
+  }
+  if (!A.pq_part) __syncthreads();
+  const float a = s_alpha;
   float acc = 0.f;
-  for (long i = bid * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)nblk * blockDim.x) {
-    float4 p = p4[i], q = q4[i], r = r4[i], d = dx4[i];
+  while (i < A.n2) {
     d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
     r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
     dx4[i] = d;
     r4[i] = r;
     acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+    i += stride;
+    if (i < A.n2) { p = p4[i]; q = q4[i]; r = r4[i]; d = dx4[i]; }
   }
   nlv::grid_reduce(acc, A, bid, nblk);
 }
@@ -130,6 +160,7 @@ struct nlinv_ctx {
   float* wtab = nullptr;      // Sobolev weight, N x N
   uint8_t* mask = nullptr;
   double* partials = nullptr;
+  double* pq_part = nullptr;  // per-block partials of Re<p, A p> of the normal-operator pass
   Scalars* sc = nullptr;
   // graph of one reconstruction
   cudaGraphExec_t graph = nullptr;
@@ -293,9 +324,11 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
-// dx += alpha p, r -= alpha q, |r|^2 -> beta
-cudaError_t q_cg_step(nlinv_ctx* c) {
+// dx += alpha p, r -= alpha q, |r|^2 -> beta; alpha from the n_pq partials of the normal-operator pass
+cudaError_t q_cg_step(nlinv_ctx* c, int n_pq) {
   KArgs a = base_args(c);
+  a.pq_part = c->pq_part;
+  a.n_pq = n_pq;
   a.reduce = nlv::RED_RR_UPDATE;
   a.p = c->p;
   a.q = c->q;
@@ -354,8 +387,10 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
   a.zsum = c->zsum;
   a.alpha = alpha;
   a.reduce = nlv::RED_PQ;
+  a.pq_only = 1;
+  a.pq_part = c->pq_part;
   if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
-  return q_cg_step(c);
+  return q_cg_step(c, row_geom(c, true).blocks);
 }
 
 // Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
@@ -551,7 +586,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
-  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + partb + scb;
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 2 * partb + scb;
   e = cudaMalloc(&c->base, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -578,6 +613,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->wtab = (float*)take(wb);
   c->mask = (uint8_t*)take(maskb);
   c->partials = (double*)take(partb);
+  c->pq_part = (double*)take(partb);
   c->sc = (Scalars*)take(scb);
 
   // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
@@ -879,10 +915,10 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     if (e == cudaSuccess) e = q_adj_col(c, c->x);
     mark();
     a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum;
-    a.alpha = al; a.reduce = nlv::RED_PQ;
+    a.alpha = al; a.reduce = nlv::RED_PQ; a.pq_only = 1; a.pq_part = c->pq_part;
     if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
     mark();
-    if (e == cudaSuccess) e = q_cg_step(c);
+    if (e == cudaSuccess) e = q_cg_step(c, row_geom(c, true).blocks);
     mark();
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
     for (int i = 0; i < K && e == cudaSuccess; ++i) {
