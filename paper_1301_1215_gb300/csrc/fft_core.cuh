@@ -203,24 +203,33 @@ template <int A, int B> struct Split {
 //   tw     table tw[k2*P1 + a] = exp(-2 pi i a k2 / (P1 P2)) (forward sign; conjugated for D = +1), in shared
 //          memory
 // Contains two __syncthreads(): every thread of the CTA must call it.
+// General form: the threads of the two steps may be mapped differently onto the lanes (a lane's exchange area is
+// the same in both).  Step 1 runs on the threads with in_ok (index in_idx < P1 of the lane whose area is sm_in),
+// step 3 on those with out_ok (index out_idx < P2, area sm_out).
 template <int P1, int P2, int D, int E>
-__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx) {
+__device__ __forceinline__ void fft_AtoB2(float2 (&v)[E], float2* sm_in, int in_idx, bool in_ok, float2* sm_out,
+                                          int out_idx, bool out_ok, const float2* tw) {
   constexpr int S = P1 + 1;
-  if (idx < P1) {
+  if (in_ok) {
     RegDFT<P2, D>::run(v);
     static_for<P2>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
-      float2 w = tw[k2 * P1 + idx];
+      float2 w = tw[k2 * P1 + in_idx];
       if (D > 0) w.y = -w.y;
-      sm[k2 * S + idx] = (k2 == 0) ? v[k2] : cmul(v[k2], w);
+      sm_in[k2 * S + in_idx] = (k2 == 0) ? v[k2] : cmul(v[k2], w);
     });
   }
   __syncthreads();
-  if (idx < P2) {
-    static_for<P1>([&](auto nc) { constexpr int n1 = decltype(nc)::value; v[n1] = sm[idx * S + n1]; });
+  if (out_ok) {
+    static_for<P1>([&](auto nc) { constexpr int n1 = decltype(nc)::value; v[n1] = sm_out[out_idx * S + n1]; });
     RegDFT<P1, D>::run(v);
   }
   __syncthreads();
+}
+
+template <int P1, int P2, int D, int E>
+__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx) {
+  fft_AtoB2<P1, P2, D>(v, sm, idx, idx < P1, sm, idx, idx < P2, tw);
 }
 
 }  // namespace nlv

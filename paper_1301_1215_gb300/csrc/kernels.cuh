@@ -308,12 +308,18 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
   constexpr int N = S::N, TL = S::TL, E = S::E;
+  static_assert(N2 == TL, "row passes assume N1 <= N2");
   const int LANES = blockDim.x / TL;
-  const int lane = threadIdx.x / TL, idx = threadIdx.x % TL;
+  // Two thread maps onto the rows of a round: layout A (N1 threads per row) packs the rows densely so that the
+  // spare warps skip the layout-A steps; layout B uses N2 = TL threads per row (every thread).
+  const int laneA = threadIdx.x / N1, idxA = threadIdx.x % N1;
+  const bool mapA = (int)threadIdx.x < LANES * N1;
+  const int laneB = threadIdx.x / N2, idxB = threadIdx.x % N2;
   const int f = A.f, Wc = A.Wc;
   float acc = 0.f;
   const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
-  float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE;
+  float2* smA = (float2*)(smem_raw + L.xch) + laneA * S::SM_LANE;
+  float2* smB = (float2*)(smem_raw + L.xch) + laneB * S::SM_LANE;
   const float2* twA = (const float2*)(smem_raw + L.tw);
   const float2* twB = twA + N;
   const float rs = rsqrtf((float)N);
@@ -323,22 +329,22 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
-  const int R = R0 + lane;                                   // row of the stacked coil planes
-  const bool active = R < r_end;
-  const int e1 = R % N;
+  const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
+  const bool activeA = mapA && RA < r_end, activeB = RB < r_end;
+  const int e1A = RA % N, e1B = RB % N;
   float2 v[E];
 
   // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
-  if (idx < N1) {
+  if (mapA) {
 #pragma unroll
     for (int m = 0; m < N2; ++m) {
-      const int e2 = idx + N1 * m;
+      const int e2 = idxA + N1 * m;
       float2 val = make_float2(0.f, 0.f);
-      if (active) {
+      if (activeA) {
         if constexpr (T::load_compact) {
-          if (in_omega(e2, N, f)) val = A.src[(size_t)R * Wc + to_compact(e2, N, f)];
+          if (in_omega(e2, N, f)) val = A.src[(size_t)RA * Wc + to_compact(e2, N, f)];
         } else if constexpr (MODE == ROW_W_IFFT) {
-          const size_t o = (size_t)R * N + e2;
+          const size_t o = (size_t)RA * N + e2;
           val = A.src[o];
           if (A.pupd) {
             const float2 rv = A.r[o];
@@ -346,8 +352,8 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
             val = make_float2(fmaf(beta, val.x, rv.x), fmaf(beta, val.y, rv.y));
           }
         } else {  // ROW_P_IFFT
-          const float2 sv = A.src[(size_t)R * N + e2];
-          val = A.mask[(size_t)e1 * N + e2] ? sv : make_float2(0.f, 0.f);
+          const float2 sv = A.src[(size_t)RA * N + e2];
+          val = A.mask[(size_t)e1A * N + e2] ? sv : make_float2(0.f, 0.f);
         }
       }
       v[m] = val;
@@ -369,60 +375,60 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 
   if constexpr (MODE == ROW_W_IFFT) {
     // write back p = r + beta p, then weight
-    const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
-    if (active && idx < N1) {
+    const float* sw = (const float*)(smem_raw + L.w) + (size_t)laneA * N;
+    if (activeA) {
 #pragma unroll
       for (int m = 0; m < N2; ++m) {
-        if (A.pupd) const_cast<float2*>(A.src)[(size_t)R * N + idx + N1 * m] = v[m];
-        v[m] = cscale(v[m], sw[idx + N1 * m] * rs);
+        if (A.pupd) const_cast<float2*>(A.src)[(size_t)RA * N + idxA + N1 * m] = v[m];
+        v[m] = cscale(v[m], sw[idxA + N1 * m] * rs);
       }
     }
   } else if constexpr (MODE == ROW_P_IFFT) {
-    if (idx < N1) {
+    if (mapA) {
 #pragma unroll
       for (int m = 0; m < N2; ++m) v[m] = cscale(v[m], rs);
     }
   }
 
   if constexpr (T::inverse_first) {
-    fft_AtoB<N1, N2, +1>(v, sm, twA, idx);
+    fft_AtoB2<N1, N2, +1>(v, smA, idxA, mapA, smB, idxB, true, twA);
     // layout B: thread b < N2 holds elements b + N2*m; keep the Omega columns
-    if (active && idx < N2) {
+    if (activeB) {
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
-        const int e2 = idx + N2 * m;
-        if (in_omega(e2, N, f)) A.dst[(size_t)R * Wc + to_compact(e2, N, f)] = v[m];
+        const int e2 = idxB + N2 * m;
+        if (in_omega(e2, N, f)) A.dst[(size_t)RB * Wc + to_compact(e2, N, f)] = v[m];
       }
     }
   } else {
-    fft_AtoB<N1, N2, -1>(v, sm, twA, idx);
-    const unsigned char* smask = smem_raw + L.mask + (size_t)lane * N;
+    fft_AtoB2<N1, N2, -1>(v, smA, idxA, mapA, smB, idxB, true, twA);
+    const unsigned char* smask = smem_raw + L.mask + (size_t)laneB * N;
     if constexpr (MODE == ROW_PSF) {
-      if (idx < N2) {
+      {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-          const float sc = (active && smask[idx + N2 * m]) ? rs * rs : 0.f;
+          const float sc = (activeB && smask[idxB + N2 * m]) ? rs * rs : 0.f;
           v[m] = cscale(v[m], sc);
         }
       }
-      fft_AtoB<N2, N1, +1>(v, sm, twB, idx);
-      if (active && idx < N1) {
+      fft_AtoB2<N2, N1, +1>(v, smB, idxB, true, smA, idxA, mapA, twB);
+      if (activeA) {
 #pragma unroll
         for (int m = 0; m < N2; ++m) {
-          const int e2 = idx + N1 * m;
-          if (in_omega(e2, N, f)) A.dst[(size_t)R * Wc + to_compact(e2, N, f)] = v[m];
+          const int e2 = idxA + N1 * m;
+          if (in_omega(e2, N, f)) A.dst[(size_t)RA * Wc + to_compact(e2, N, f)] = v[m];
         }
       }
     } else {
-      const float* sw = (const float*)(smem_raw + L.w) + (size_t)lane * N;
+      const float* sw = (const float*)(smem_raw + L.w) + (size_t)laneB * N;
       // staged rows of y; p, or x and x_ref, loaded into registers before any store
-      const float2* scp = (const float2*)(smem_raw + L.cplx) + (size_t)lane * N;
+      const float2* scp = (const float2*)(smem_raw + L.cplx) + (size_t)laneB * N;
       constexpr int NV = (MODE == ROW_FFT_W_RHS) ? 2 : (MODE == ROW_FFT_W_NORMAL) ? 1 : 0;
       float2 a0[NV ? N1 : 1], a1[NV == 2 ? N1 : 1];
-      if (NV && active && idx < N2) {
+      if (NV && activeB) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-          const size_t oc = (size_t)N * N + (size_t)R * N + idx + N2 * m;
+          const size_t oc = (size_t)N * N + (size_t)RB * N + idxB + N2 * m;
           if constexpr (MODE == ROW_FFT_W_NORMAL) a0[m] = A.p[oc];
           if constexpr (MODE == ROW_FFT_W_RHS) {
             a0[m] = A.x[oc];
@@ -430,11 +436,11 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
           }
         }
       }
-      if (active && idx < N2) {
+      if (activeB) {
 #pragma unroll
         for (int m = 0; m < N1; ++m) {
-          const int e2 = idx + N2 * m;
-          const size_t o = (size_t)R * N + e2;
+          const int e2 = idxB + N2 * m;
+          const size_t o = (size_t)RB * N + e2;
           if constexpr (MODE == ROW_FFT_P_OUT) {
             A.dst[o] = smask[e2] ? cscale(v[m], rs) : make_float2(0.f, 0.f);
           } else if constexpr (MODE == ROW_FFT_RESID) {

@@ -132,6 +132,9 @@ __global__ void add_batch(const nlv::BatchArgs B) {
 }
 
 constexpr int kVecThreads = 256;
+#ifndef NLV_VEC_BLOCKS_PER_SM
+#define NLV_VEC_BLOCKS_PER_SM 4   // blocks per SM of the vector passes
+#endif
 constexpr int kProfileKernels = 6;   // kernels of one CG iteration, in the order nlinv_profile_cg reports them
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -537,7 +540,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   if (const char* v = std::getenv("NLINV_PDL")) c->pdl = std::strcmp(v, "0") != 0;
   c->sms = std::max(1, sms);
-  c->vec_blocks = c->sms * 4;
+  c->vec_blocks = c->sms * NLV_VEC_BLOCKS_PER_SM;
   if (batch_lanes > 0)   // a frame of a batch: vector passes get blocks in proportion to its size
     c->vec_blocks = (int)std::min<long>(c->vec_blocks, std::max<long>(1, c->vec / 2 / (kVecThreads * 8)));
 
