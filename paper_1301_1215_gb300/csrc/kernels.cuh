@@ -236,6 +236,10 @@ __host__ __device__ inline RowSmem row_smem(int mode, int N, int lanes, int sm_l
   return L;
 }
 
+#ifndef NLV_COL_C
+#define NLV_COL_C 8
+#endif
+
 // Row passes run kRowCtasPerSM blocks per SM; a block holds up to kRowMaxThreads threads (whole lanes of TL
 // threads) and loops over its share of rows when they do not fit at once.
 constexpr int kRowMaxThreads = 320;
@@ -515,43 +519,52 @@ __host__ __device__ inline ColSmem col_smem(int mode, int N, int C, int sm_lane,
   return L;
 }
 
-// Column passes: a block takes C consecutive columns of the flat index g = j*Wc + cc over all coils (C chosen at
-// launch so that the columns split evenly over the SMs), TL threads per column.
-constexpr int kColMaxLanes = 16;
 template <int N1, int N2> struct ColCfg {
   using S = Split<N1, N2>;
-  static constexpr int THREADS = kColMaxLanes * S::TL;
+  static constexpr int C = NLV_COL_C;               // adjacent compact columns per block
+  static constexpr int THREADS = C * S::TL;
+  static_assert(C % 2 == 0, "column staging copies pairs of complex values");
 };
 
-// Stages the Omega rows of the block's columns g0 .. g0+C-1 (flat over coils) of a compact per-coil array
-// (J x Wc x Wc) or, for a natural N x N plane shared by all coils, of the matching natural columns.
-__device__ __forceinline__ void stage_flat_compact(float2* sdst, const float2* arr, int g0, int C, int Wc, int total) {
-  for (int i = threadIdx.x; i < Wc * C; i += blockDim.x) {
-    const int cr = i / C, l = i % C, g = g0 + l;
-    if (g < total) cp_async8(sdst + (size_t)cr * C + l, arr + ((size_t)(g / Wc) * Wc + cr) * Wc + g % Wc);
+// Stages Omega rows of C columns starting at compact column cc0 of a compact (Wc x Wc per coil) array.
+__device__ __forceinline__ void stage_compact_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc) {
+  const int cpr = C / 2;                               // 16-byte chunks per row segment
+  for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
+    const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
+    if (cc < Wc) cp_async16(sdst + (size_t)cr * C + 2 * k, plane + (size_t)cr * Wc + cc);
   }
 }
-__device__ __forceinline__ void stage_flat_natural(float2* sdst, const float2* plane, int g0, int C, int Wc, int N,
-                                                   int f, int total) {
-  for (int i = threadIdx.x; i < Wc * C; i += blockDim.x) {
-    const int cr = i / C, l = i % C, g = g0 + l;
-    if (g < total)
-      cp_async8(sdst + (size_t)cr * C + l, plane + (size_t)to_natural(cr, N, f) * N + to_natural(g % Wc, N, f));
+// Same for a natural N x N plane (rows and columns mapped from compact to natural indices).
+__device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc, int N,
+                                                   int f) {
+  if ((f & 1) == 0) {                                  // compact pairs (2k, 2k+1) stay adjacent in natural order
+    const int cpr = C / 2;
+    for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
+      const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
+      if (cc < Wc)
+        cp_async16(sdst + (size_t)cr * C + 2 * k,
+                   plane + (size_t)to_natural(cr, N, f) * N + to_natural(cc, N, f));
+    }
+  } else {
+    for (int i = threadIdx.x; i < Wc * C; i += blockDim.x) {
+      const int cr = i / C, k = i % C, cc = cc0 + k;
+      if (cc < Wc)
+        cp_async8(sdst + (size_t)cr * C + k, plane + (size_t)to_natural(cr, N, f) * N + to_natural(cc, N, f));
+    }
   }
 }
 
 template <int N1, int N2, int MODE>
 __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
-  constexpr int N = S::N, E = S::E;
-  const int C = blockDim.x / S::TL;
+  constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
   const int f = A.f, Wc = A.Wc;
-  const int total = A.nrows * Wc;                     // columns of all coils
-  const int g0 = bid * C, g = g0 + lane;
-  const bool active = g < total;
-  const int j = active ? g / Wc : 0;
-  const int cc = active ? g % Wc : 0;
+  const int strips = (Wc + C - 1) / C;
+  const int j = bid / strips;
+  const int cc0 = (bid % strips) * C;
+  const int cc = cc0 + lane;
+  const bool active = cc < Wc && j < A.nrows;
   const int x2 = to_natural(cc, N, f);
   const ColSmem L = col_smem(MODE, N, C, S::SM_LANE_COL, Wc);
   float2* sm = (float2*)(smem_raw + L.xch) + lane * S::SM_LANE_COL;
@@ -584,16 +597,16 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
   // ---- staged side inputs (Omega rows of this block's columns) and twiddles
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
-  {
+  if (j < A.nrows) {
     float2* sd = (float2*)(smem_raw + L.side);
     const size_t sstride = (size_t)Wc * C;
     if constexpr (MODE == COL_IFFT_PROD_FFT || MODE == COL_IFFT_ADJ_FFT) {
-      stage_flat_compact(sd, A.coil, g0, C, Wc, total);
-      stage_flat_natural(sd + sstride, A.rho, g0, C, Wc, N, f, total);
+      stage_compact_cols(sd, A.coil + (size_t)j * Wc * Wc, cc0, C, Wc);
+      stage_natural_cols(sd + sstride, A.rho, cc0, C, Wc, N, f);
     }
     if constexpr (MODE == COL_IFFT_PROD_FFT) {
-      stage_flat_natural(sd + 2 * sstride, A.drho, g0, C, Wc, N, f, total);
-      if (A.pupd) stage_flat_natural(sd + 3 * sstride, A.r, g0, C, Wc, N, f, total);
+      stage_natural_cols(sd + 2 * sstride, A.drho, cc0, C, Wc, N, f);
+      if (A.pupd) stage_natural_cols(sd + 3 * sstride, A.r, cc0, C, Wc, N, f);
     }
   }
   cp_async_wait_all();
@@ -718,6 +731,7 @@ __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass_batch(const 
 struct SizeKernels {
   int N1, N2;
   int tl;                   // threads per lane
+  int col_lanes, col_threads;
   int sm_lane;              // shared float2 per lane for one exchange (row passes)
   int sm_lane_col;          // the same for column passes (bank-conflict padding)
   const void* row[NUM_ROW_MODES];
@@ -725,9 +739,7 @@ struct SizeKernels {
   const void* row_batch[NUM_ROW_MODES];
   const void* col_batch[NUM_COL_MODES];
   size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
-  size_t col_smem(int mode, int Wc, int lanes) const {
-    return nlv::col_smem(mode, N1 * N2, lanes, sm_lane_col, Wc).total;
-  }
+  size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane_col, Wc).total; }
 };
 
 // Launch geometry of a row pass: `blocks` blocks of `lanes` lanes, each taking rows_per_cta rows (and rho_per_cta
@@ -754,6 +766,8 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.N1 = N1;
   s.N2 = N2;
   s.tl = Split<N1, N2>::TL;
+  s.col_lanes = ColCfg<N1, N2>::C;
+  s.col_threads = ColCfg<N1, N2>::THREADS;
   s.sm_lane = Split<N1, N2>::SM_LANE;
   s.sm_lane_col = Split<N1, N2>::SM_LANE_COL;
   s.row[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT>;

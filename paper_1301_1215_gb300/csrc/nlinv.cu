@@ -153,7 +153,6 @@ struct nlinv_ctx {
   int device = 0;
   int vec_blocks = 0;         // grid of the vector kernels
   int sms = 0;                // streaming multiprocessors of the device
-  int smem_limit = 48 * 1024; // opt-in shared memory per block of the device
   int row_ctas_per_sm = nlv::kRowCtasPerSM;   // blocks per SM of the row passes
   // workspace (one allocation)
   void* base = nullptr;
@@ -236,22 +235,9 @@ nlv::RowGrid row_geom(const nlinv_ctx* c, bool with_rho) {
   return nlv::row_grid(c->k, c->J * c->N, with_rho ? c->plane : 0, c->sms, c->row_ctas_per_sm);
 }
 
-// Column lanes per block: the J*Wc columns split evenly over the SMs (a fixed 8 for batch frames, whose blocks of
-// one grid side must have equal shapes).
-int col_lanes(const nlinv_ctx* c) {
-  int C = 8;
-  if (c->batch_lanes <= 0) {
-    const int total = c->J * c->Wc;
-    C = std::max(1, std::min(nlv::kColMaxLanes, (total + c->sms - 1) / c->sms));
-  }
-  // the widest column pass (four staged side arrays) must fit in the device's shared memory
-  while (C > 1 && c->k->col_smem(nlv::COL_IFFT_PROD_FFT, c->Wc, C) + 1024 > (size_t)c->smem_limit) --C;
-  return C;
-}
-
 int col_blocks(const nlinv_ctx* c) {
-  const int C = col_lanes(c);
-  return (c->J * c->Wc + C - 1) / C;
+  const int C = c->k->col_lanes;
+  return c->J * ((c->Wc + C - 1) / C);
 }
 
 // Launches with programmatic stream serialisation (see pdl_enter in kernels.cuh): the next pass is scheduled while
@@ -289,8 +275,7 @@ cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
 cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J;
   void* args[] = {&a};
-  const int C = col_lanes(c);
-  return launch(c, c->k->col[mode], col_blocks(c), C * c->k->tl, c->k->col_smem(mode, c->Wc, C), args);
+  return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
 }
 
 // c_j = W^-1 chat_j on Omega, for the coil planes of x (1+J planes).
@@ -562,7 +547,6 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   // dynamic shared memory above the 48 KB default, within the device's opt-in limit
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  c->smem_limit = std::max(48 * 1024, smem_optin);
   // (the limit is raised to the device maximum so that contexts with different fov can share the kernels)
   std::string smem_err;
   auto allow = [&](const void* fn, size_t need) {
@@ -583,8 +567,8 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
     if (smem_err.empty()) allow(c->k->row_batch[m], c->k->row_smem(m, lanes_max));
   }
   for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) {
-    allow(c->k->col[m], c->k->col_smem(m, c->Wc, col_lanes(c)));
-    if (smem_err.empty()) allow(c->k->col_batch[m], c->k->col_smem(m, c->Wc, col_lanes(c)));
+    allow(c->k->col[m], c->k->col_smem(m, c->Wc));
+    if (smem_err.empty()) allow(c->k->col_batch[m], c->k->col_smem(m, c->Wc));
   }
   if (!smem_err.empty()) {
     cudaGetLastError();

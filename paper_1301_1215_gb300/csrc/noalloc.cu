@@ -7,7 +7,6 @@
 // scratch -- the Omega-column transform buffer, the coil maps, the twiddle and Sobolev tables -- in one
 // file-scope __device__ array of fixed size (kScratchBytes).  Every GPU that loads the library holds that array
 // until the process exits.
-#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -158,8 +157,7 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const nlv::RowGrid rg = nlv::row_grid(k, J * N, 0, sms < 1 ? 1 : sms, nlv::kRowCtasPerSM);
-  const int clanes = std::max(1, std::min(nlv::kColMaxLanes, (J * Wc + (sms < 1 ? 1 : sms) - 1) / (sms < 1 ? 1 : sms)));
-  const int cols = (J * Wc + clanes - 1) / clanes;
+  const int cols = J * ((Wc + k->col_lanes - 1) / k->col_lanes);
   const float2* xv = (const float2*)x;
 
   nlv::KArgs a1 = a;                        // T = FFT^-1_row(w chat_j), Omega columns
@@ -167,12 +165,10 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   e = launch(k->row[nlv::ROW_W_IFFT], rg.blocks, rg.lanes * k->tl, k->row_smem(nlv::ROW_W_IFFT, rg.lanes), st, a1);
   nlv::KArgs a2 = a;                        // c_j = Omega rows of FFT^-1_col(T)
   a2.src = T; a2.dst = coil; a2.nrows = J;
-  if (e == cudaSuccess)
-    e = launch(k->col[nlv::COL_IFFT_C], cols, clanes * k->tl, k->col_smem(nlv::COL_IFFT_C, Wc, clanes), st, a2);
+  if (e == cudaSuccess) e = launch(k->col[nlv::COL_IFFT_C], cols, k->col_threads, k->col_smem(nlv::COL_IFFT_C, Wc), st, a2);
   nlv::KArgs a3 = a;                        // T = FFT_col(M rho c_j)
   a3.rho = xv; a3.coil = coil; a3.dst = T; a3.nrows = J;
-  if (e == cudaSuccess)
-    e = launch(k->col[nlv::COL_PROD_FFT], cols, clanes * k->tl, k->col_smem(nlv::COL_PROD_FFT, Wc, clanes), st, a3);
+  if (e == cudaSuccess) e = launch(k->col[nlv::COL_PROD_FFT], cols, k->col_threads, k->col_smem(nlv::COL_PROD_FFT, Wc), st, a3);
   nlv::KArgs a4 = a;                        // y = P FFT_row(T)
   a4.src = T; a4.dst = (float2*)y_out; a4.mask = mask; a4.nrows = J * N; a4.rows_per_cta = rg.rows_per_cta;
   if (e == cudaSuccess)
