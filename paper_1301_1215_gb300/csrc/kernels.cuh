@@ -21,14 +21,14 @@ enum Reduce : int {
   RED_RESID = 1,      // Scalars::resid[slot] = sqrt(sum)       (|y - F x_n|)
   RED_RR_INIT = 2,    // Scalars::rr = sum                      (|b|^2 at the start of CG)
   RED_PQ = 3,         // Scalars::alpha = rr / sum              (sum = Re<p, A p>)
-  RED_RR_UPDATE = 4,  // Scalars::beta = sum / rr, rr = sum     (|r_new|^2)
 };
 
 constexpr int kMaxNewton = 64;
 
 // Scalars of the CG and Newton iterations, kept in device memory (FP64).
 struct Scalars {
-  double rr;                     // |r|^2 of the current CG residual
+  double rr;                     // |r|^2 of the current CG residual (numerator of alpha)
+  double rr_prev;                // |r|^2 of the previous CG residual (denominator of the next beta)
   double alpha;                  // CG step length
   double beta;                   // CG direction update
   double pq;                     // last Re<p, A p>
@@ -74,6 +74,10 @@ struct KArgs {
   double* pq_part;
   int n_pq;
   int pq_only;
+  // |r|^2 likewise: the CG step writes one partial per block into rr_part, and the first pass of the next CG
+  // iteration (its one consumer) adds the n_rr partials to form beta.  rr_part = NULL: beta from Scalars.
+  double* rr_part;
+  int n_rr;
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -133,12 +137,6 @@ __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slo
       if (!isfinite(total) || !isfinite(rr)) sc->flags |= 1;
       else if (rr != 0.0 && total > 0.0) a = rr / total;
       sc->alpha = a;
-      break;
-    }
-    case RED_RR_UPDATE: {
-      double rr = sc->rr;
-      sc->beta = (rr != 0.0) ? total / rr : 0.0;
-      sc->rr = total;
       break;
     }
     default: sc->last = total; break;
@@ -327,6 +325,28 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  // beta of the direction update p = r + beta p: from the |r|^2 partials of the CG step before (same order in
+  // every block; block 0 publishes |r|^2 and beta for the CG step and the later passes of this iteration)
+  __shared__ float s_beta;
+  if constexpr (MODE == ROW_W_IFFT) {
+    if (A.pupd) {
+      if (A.rr_part) {
+        __shared__ double red[32];
+        double t = 0.0;
+        for (int k = threadIdx.x; k < A.n_rr; k += blockDim.x) t += A.rr_part[k];
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) {
+          const double rp = A.sc->rr_prev;
+          const double b = (rp != 0.0) ? t / rp : 0.0;
+          s_beta = (float)b;
+          if (bid == 0) { A.sc->rr = t; A.sc->beta = b; }
+        }
+      } else if (threadIdx.x == 0) {
+        s_beta = cg_beta(A);
+      }
+      __syncthreads();
+    }
+  }
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
@@ -348,8 +368,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
           val = A.src[o];
           if (A.pupd) {
             const float2 rv = A.r[o];
-            const float beta = cg_beta(A);
-            val = make_float2(fmaf(beta, val.x, rv.x), fmaf(beta, val.y, rv.y));
+            val = make_float2(fmaf(s_beta, val.x, rv.x), fmaf(s_beta, val.y, rv.y));
           }
         } else {  // ROW_P_IFFT
           const float2 sv = A.src[(size_t)RA * N + e2];

@@ -32,7 +32,7 @@ namespace {
 thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
-// dx += alpha p; r -= alpha q; |r|^2 -> RED_RR_UPDATE, over this block's share of the A.n2 float4.
+// dx += alpha p; r -= alpha q; partial of |r|^2 -> rr_part[bid], over this block's share of the A.n2 float4.
 __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
   const float4* __restrict__ p4 = (const float4*)A.p;
   const float4* __restrict__ q4 = (const float4*)A.q;
@@ -58,7 +58,7 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
         } else if (rr != 0.0 && t > 0.0) {
           a = rr / t;
         }
-        if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; }
+        if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; A.sc->rr_prev = rr; }
         s_alpha = (float)a;
       }
     }
@@ -78,7 +78,9 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
     i += stride;
     if (i < A.n2) { p = p4[i]; q = q4[i]; r = r4[i]; d = dx4[i]; }
   }
-  nlv::grid_reduce(acc, A, bid, nblk);
+  __shared__ double red[32];
+  const double s = nlv::block_sum((double)acc, red);
+  if (threadIdx.x == 0) A.rr_part[bid] = s;
 }
 
 // x += dx (x = A.dst)
@@ -164,6 +166,7 @@ struct nlinv_ctx {
   uint8_t* mask = nullptr;
   double* partials = nullptr;
   double* pq_part = nullptr;  // per-block partials of Re<p, A p> of the normal-operator pass
+  double* rr_part = nullptr;  // per-block partials of |r|^2 of the CG step
   Scalars* sc = nullptr;
   // graph of one reconstruction
   cudaGraphExec_t graph = nullptr;
@@ -327,12 +330,12 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
-// dx += alpha p, r -= alpha q, |r|^2 -> beta; alpha from the n_pq partials of the normal-operator pass
+// dx += alpha p, r -= alpha q, partials of |r|^2; alpha from the n_pq partials of the normal-operator pass
 cudaError_t q_cg_step(nlinv_ctx* c, int n_pq) {
   KArgs a = base_args(c);
   a.pq_part = c->pq_part;
   a.n_pq = n_pq;
-  a.reduce = nlv::RED_RR_UPDATE;
+  a.rr_part = c->rr_part;
   a.p = c->p;
   a.q = c->q;
   a.r = c->r;
@@ -354,15 +357,19 @@ cudaError_t q_add(nlinv_ctx* c) {
 
 // One CG iteration on (DF^H DF + alpha) for linearisation point x.  The direction update p = r + beta p of the
 // previous iteration is folded into the passes that first read p (beta = 0 right after the right-hand side).
-//   K1 row  p_c = r_c + beta p_c; T = W^-1 p_c (first axis)
+//   K1 row  beta from the |r|^2 partials of K6 before; p_c = r_c + beta p_c; T = W^-1 p_c (first axis)
 //   K2 col  drho = r_rho + beta p_rho; T = FFT_col(M (drho c_j + rho W^-1 p_c))
 //   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> -> alpha
-//   K6      dx += alpha p, r -= alpha q, |r|^2 -> beta
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha) {
+//   K6      dx += alpha p, r -= alpha q, per-block partials of |r|^2
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
   KArgs a = base_args(c);
   a.src = c->p + c->plane;
   a.r = c->r + c->plane;
   a.pupd = 1;
+  if (!first) {
+    a.rr_part = c->rr_part;
+    a.n_rr = c->vec_blocks;
+  }
   a.dst = c->T;
   cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
   if (e != cudaSuccess) return e;
@@ -438,7 +445,7 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     a.reduce = nlv::RED_RR_INIT;
     if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
     for (int i = 0; i < P.cg_iters; ++i)
-      if ((e = q_cg_iter(c, c->x, al)) != cudaSuccess) return e;
+      if ((e = q_cg_iter(c, c->x, al, i == 0)) != cudaSuccess) return e;
     if ((e = q_add(c)) != cudaSuccess) return e;
     c->last_alpha = alpha;
     alpha = std::max(alpha * P.alpha_q, P.alpha_min);
@@ -589,7 +596,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
-  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 2 * partb + scb;
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 3 * partb + scb;
   e = cudaMalloc(&c->base, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -617,6 +624,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->mask = (uint8_t*)take(maskb);
   c->partials = (double*)take(partb);
   c->pq_part = (double*)take(partb);
+  c->rr_part = (double*)take(partb);
   c->sc = (Scalars*)take(scb);
 
   // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
@@ -906,6 +914,7 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     mark();
     KArgs a = base_args(c);
     a.src = c->p + c->plane; a.r = c->r + c->plane; a.pupd = 1; a.dst = c->T;
+    a.rr_part = c->rr_part; a.n_rr = c->vec_blocks;
     if (e == cudaSuccess) e = row(c, nlv::ROW_W_IFFT, a);
     mark();
     a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.r = c->r; a.pupd = 1;
