@@ -104,23 +104,42 @@ __device__ __forceinline__ float sobolev_w(int k1, int k2, const KArgs& A) {
 __device__ __forceinline__ float cg_beta(const KArgs& A) { return (float)A.sc->beta; }
 
 // ----------------------------------------------------------------------------------------- reductions ----
-__device__ __forceinline__ double warp_sum(double v) {
+// Butterfly sum over the lanes of this warp that exist: lanes 0..cnt-1 (a block's last warp may be partial, and a
+// row block can be narrower than a warp).  Only those lanes take part in the shuffles; a partner lane that does not
+// exist counts as 0.  Valid in lane 0.
+__device__ __forceinline__ double warp_sum(double v, int cnt = 32) {
+  if (cnt >= 32) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+  const unsigned mask = (1u << cnt) - 1u;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double w = __shfl_xor_sync(mask, v, o);
+    if ((lane ^ o) < cnt) v += w;
+  }
   return v;
+}
+
+// Lanes of the calling thread's warp that exist in this block.
+__device__ __forceinline__ int warp_lanes() {
+  const int rest = (int)blockDim.x - (int)(threadIdx.x & ~31u);
+  return rest < 32 ? rest : 32;
 }
 
 // Deterministic block sum (fixed tree), result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  v = warp_sum(v);
+  v = warp_sum(v, warp_lanes());
   __syncthreads();
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double s = 0.0;
   if (warp == 0) {
     s = lane < nw ? red[lane] : 0.0;
-    s = warp_sum(s);
+    s = warp_sum(s, warp_lanes());
   }
   return s;
 }

@@ -47,9 +47,10 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
   __shared__ float s_alpha;
   if (A.pq_part) {
     if (threadIdx.x < 32) {
+      const int nl = nlv::warp_lanes();
       double t = 0.0;
-      for (int k = threadIdx.x; k < A.n_pq; k += 32) t += A.pq_part[k];
-      t = nlv::warp_sum(t);
+      for (int k = threadIdx.x; k < A.n_pq; k += nl) t += A.pq_part[k];
+      t = nlv::warp_sum(t, nl);
       if (threadIdx.x == 0) {
         const double rr = A.sc->rr;
         double a = 0.0;
@@ -359,9 +360,10 @@ cudaError_t q_add(nlinv_ctx* c) {
 // previous iteration is folded into the passes that first read p (beta = 0 right after the right-hand side).
 //   K1 row  beta from the |r|^2 partials of K6 before; p_c = r_c + beta p_c; T = W^-1 p_c (first axis)
 //   K2 col  drho = r_rho + beta p_rho; T = FFT_col(M (drho c_j + rho W^-1 p_c))
-//   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> -> alpha
-//   K6      dx += alpha p, r -= alpha q, per-block partials of |r|^2
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
+//   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> partials
+//   K6      alpha from the K5 partials; dx += alpha p, r -= alpha q, per-block partials of |r|^2
+// The steps are separate functions so that nlinv_profile_cg times exactly what a reconstruction launches.
+cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
   KArgs a = base_args(c);
   a.src = c->p + c->plane;
   a.r = c->r + c->plane;
@@ -371,9 +373,11 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
     a.n_rr = c->vec_blocks;
   }
   a.dst = c->T;
-  cudaError_t e = row(c, nlv::ROW_W_IFFT, a);
-  if (e != cudaSuccess) return e;
-  a = base_args(c);
+  return row(c, nlv::ROW_W_IFFT, a);
+}
+
+cudaError_t q_cg_k2(nlinv_ctx* c, const float2* x) {
+  KArgs a = base_args(c);
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -381,14 +385,19 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
   a.r = c->r;
   a.pupd = 1;
   a.coil = c->coil;
-  if ((e = col(c, nlv::COL_IFFT_PROD_FFT, a)) != cudaSuccess) return e;
-  a = base_args(c);
+  return col(c, nlv::COL_IFFT_PROD_FFT, a);
+}
+
+cudaError_t q_cg_k3(nlinv_ctx* c) {
+  KArgs a = base_args(c);
   a.src = c->T;
   a.dst = c->T;
   a.mask = c->mask;
-  if ((e = row(c, nlv::ROW_PSF, a)) != cudaSuccess) return e;
-  if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
-  a = base_args(c);
+  return row(c, nlv::ROW_PSF, a);
+}
+
+cudaError_t q_cg_k5(nlinv_ctx* c, float alpha) {
+  KArgs a = base_args(c);
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
@@ -399,7 +408,16 @@ cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
   a.reduce = nlv::RED_PQ;
   a.pq_only = 1;
   a.pq_part = c->pq_part;
-  if ((e = row(c, nlv::ROW_FFT_W_NORMAL, a)) != cudaSuccess) return e;
+  return row(c, nlv::ROW_FFT_W_NORMAL, a);
+}
+
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
+  cudaError_t e;
+  if ((e = q_cg_k1(c, first)) != cudaSuccess) return e;
+  if ((e = q_cg_k2(c, x)) != cudaSuccess) return e;
+  if ((e = q_cg_k3(c)) != cudaSuccess) return e;
+  if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
+  if ((e = q_cg_k5(c, alpha)) != cudaSuccess) return e;
   return q_cg_step(c, row_geom(c, true).blocks);
 }
 
@@ -912,23 +930,15 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
     int k = 0;
     auto mark = [&]() { if (e == cudaSuccess) e = cudaEventRecord(ev[k++], c->stream); };
     mark();
-    KArgs a = base_args(c);
-    a.src = c->p + c->plane; a.r = c->r + c->plane; a.pupd = 1; a.dst = c->T;
-    a.rr_part = c->rr_part; a.n_rr = c->vec_blocks;
-    if (e == cudaSuccess) e = row(c, nlv::ROW_W_IFFT, a);
+    if (e == cudaSuccess) e = q_cg_k1(c, false);
     mark();
-    a = base_args(c); a.src = c->T; a.dst = c->T; a.rho = c->x; a.drho = c->p; a.r = c->r; a.pupd = 1;
-    a.coil = c->coil;
-    if (e == cudaSuccess) e = col(c, nlv::COL_IFFT_PROD_FFT, a);
+    if (e == cudaSuccess) e = q_cg_k2(c, c->x);
     mark();
-    a = base_args(c); a.src = c->T; a.dst = c->T; a.mask = c->mask;
-    if (e == cudaSuccess) e = row(c, nlv::ROW_PSF, a);
+    if (e == cudaSuccess) e = q_cg_k3(c);
     mark();
     if (e == cudaSuccess) e = q_adj_col(c, c->x);
     mark();
-    a = base_args(c); a.src = c->T; a.dst = c->q; a.p = c->p; a.r = c->r; a.pupd = 1; a.zsum = c->zsum;
-    a.alpha = al; a.reduce = nlv::RED_PQ; a.pq_only = 1; a.pq_part = c->pq_part;
-    if (e == cudaSuccess) e = row(c, nlv::ROW_FFT_W_NORMAL, a);
+    if (e == cudaSuccess) e = q_cg_k5(c, al);
     mark();
     if (e == cudaSuccess) e = q_cg_step(c, row_geom(c, true).blocks);
     mark();
