@@ -344,34 +344,21 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
   stage_bytes(smem_raw + L.tw, A.twA, N * 8);
   stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
-  // beta of the direction update p = r + beta p: from the |r|^2 partials of the CG step before (same order in
-  // every block; block 0 publishes |r|^2 and beta for the CG step and the later passes of this iteration)
-  __shared__ float s_beta;
-  if constexpr (MODE == ROW_W_IFFT) {
-    if (A.pupd) {
-      if (A.rr_part) {
-        __shared__ double red[32];
-        double t = 0.0;
-        for (int k = threadIdx.x; k < A.n_rr; k += blockDim.x) t += A.rr_part[k];
-        t = block_sum(t, red);
-        if (threadIdx.x == 0) {
-          const double rp = A.sc->rr_prev;
-          const double b = (rp != 0.0) ? t / rp : 0.0;
-          s_beta = (float)b;
-          if (bid == 0) { A.sc->rr = t; A.sc->beta = b; }
-        }
-      } else if (threadIdx.x == 0) {
-        s_beta = cg_beta(A);
-      }
-      __syncthreads();
-    }
-  }
+  __shared__ float s_beta;       // beta of the direction update p = r + beta p (ROW_W_IFFT with pupd)
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
   const bool activeA = mapA && RA < r_end, activeB = RB < r_end;
   const int e1A = RA % N, e1B = RB % N;
   float2 v[E];
+
+  // ---- direction update: the rows of r go to the exchange buffer (natural order, pitch N) while p is loaded
+  if constexpr (MODE == ROW_W_IFFT) {
+    if (A.pupd) {
+      for (int l = 0; l < LANES && R0 + l < r_end; ++l)
+        stage_bytes(smem_raw + L.xch + (size_t)l * N * 8, A.r + (size_t)(R0 + l) * N, N * 8);
+    }
+  }
 
   // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
   if (mapA) {
@@ -383,12 +370,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
         if constexpr (T::load_compact) {
           if (in_omega(e2, N, f)) val = A.src[(size_t)RA * Wc + to_compact(e2, N, f)];
         } else if constexpr (MODE == ROW_W_IFFT) {
-          const size_t o = (size_t)RA * N + e2;
-          val = A.src[o];
-          if (A.pupd) {
-            const float2 rv = A.r[o];
-            val = make_float2(fmaf(s_beta, val.x, rv.x), fmaf(s_beta, val.y, rv.y));
-          }
+          val = A.src[(size_t)RA * N + e2];
         } else {  // ROW_P_IFFT
           const float2 sv = A.src[(size_t)RA * N + e2];
           val = A.mask[(size_t)e1A * N + e2] ? sv : make_float2(0.f, 0.f);
@@ -408,19 +390,45 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
     if constexpr (MODE == ROW_FFT_RESID)
       stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
   }
+  // beta from the |r|^2 partials of the CG step before, while the loads above are in flight (same order in every
+  // block; block 0 publishes |r|^2 and beta for the CG step and the later passes of this iteration)
+  if constexpr (MODE == ROW_W_IFFT) {
+    if (A.pupd && R0 == r_begin) {
+      if (A.rr_part) {
+        __shared__ double red[32];
+        double t = 0.0;
+        for (int k = threadIdx.x; k < A.n_rr; k += blockDim.x) t += A.rr_part[k];
+        t = block_sum(t, red);
+        if (threadIdx.x == 0) {
+          const double rp = A.sc->rr_prev;
+          const double b = (rp != 0.0) ? t / rp : 0.0;
+          s_beta = (float)b;
+          if (bid == 0) { A.sc->rr = t; A.sc->beta = b; }
+        }
+      } else if (threadIdx.x == 0) {
+        s_beta = cg_beta(A);
+      }
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
 
   if constexpr (MODE == ROW_W_IFFT) {
-    // write back p = r + beta p, then weight
+    // p = r + beta p (r from the exchange buffer) written back, then weight
     const float* sw = (const float*)(smem_raw + L.w) + (size_t)laneA * N;
+    const float2* sr = (const float2*)(smem_raw + L.xch) + (size_t)laneA * N;
     if (activeA) {
 #pragma unroll
       for (int m = 0; m < N2; ++m) {
-        if (A.pupd) const_cast<float2*>(A.src)[(size_t)RA * N + idxA + N1 * m] = v[m];
+        if (A.pupd) {
+          const float2 rv = sr[idxA + N1 * m];
+          v[m] = make_float2(fmaf(s_beta, v[m].x, rv.x), fmaf(s_beta, v[m].y, rv.y));
+          const_cast<float2*>(A.src)[(size_t)RA * N + idxA + N1 * m] = v[m];
+        }
         v[m] = cscale(v[m], sw[idxA + N1 * m] * rs);
       }
     }
+    if (A.pupd) __syncthreads();   // the exchange below overwrites the staged rows of r
   } else if constexpr (MODE == ROW_P_IFFT) {
     if (mapA) {
 #pragma unroll

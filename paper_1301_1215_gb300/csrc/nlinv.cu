@@ -33,53 +33,59 @@ thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
 // dx += alpha p; r -= alpha q; partial of |r|^2 -> rr_part[bid], over this block's share of the A.n2 float4.
+__device__ __forceinline__ void cg_step_update(float4& d, float4& r, const float4& p, const float4& q, float a,
+                                               float& acc) {
+  d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
+  r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
+  acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+}
+
 __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
   const float4* __restrict__ p4 = (const float4*)A.p;
   const float4* __restrict__ q4 = (const float4*)A.q;
   float4* __restrict__ r4 = (float4*)A.r;
   float4* __restrict__ dx4 = (float4*)A.dx;
-  // first group of operands loaded while warp 0 forms alpha = |r|^2 / Re<p, A p> from the partials of the
-  // normal-operator pass (same order in every block; empty step at the rounding floor, flag on non-finite values)
+  // Two groups of operands per thread in flight: the first two are loaded while the block forms
+  // alpha = |r|^2 / Re<p, A p> from the partials of the normal-operator pass (every block sums them in the same
+  // fixed order; empty step at the rounding floor, flag on non-finite values).
   const long stride = (long)nblk * blockDim.x;
   long i = bid * (long)blockDim.x + threadIdx.x;
-  float4 p, q, r, d;
-  if (i < A.n2) { p = p4[i]; q = q4[i]; r = r4[i]; d = dx4[i]; }
+  float4 p0, q0, r0, d0, p1, q1, r1, d1;
+  if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
+  if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
   __shared__ float s_alpha;
-  if (A.pq_part) {
-    if (threadIdx.x < 32) {
-      const int nl = nlv::warp_lanes();
-      double t = 0.0;
-      for (int k = threadIdx.x; k < A.n_pq; k += nl) t += A.pq_part[k];
-      t = nlv::warp_sum(t, nl);
-      if (threadIdx.x == 0) {
-        const double rr = A.sc->rr;
-        double a = 0.0;
-        if (!isfinite(t) || !isfinite(rr)) {
-          if (bid == 0) A.sc->flags |= 1;
-        } else if (rr != 0.0 && t > 0.0) {
-          a = rr / t;
-        }
-        if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; A.sc->rr_prev = rr; }
-        s_alpha = (float)a;
-      }
+  __shared__ double red[32];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < A.n_pq; k += blockDim.x) t += A.pq_part[k];
+  t = nlv::block_sum(t, red);
+  if (threadIdx.x == 0) {
+    const double rr = A.sc->rr;
+    double a = 0.0;
+    if (!isfinite(t) || !isfinite(rr)) {
+      if (bid == 0) A.sc->flags |= 1;
+    } else if (rr != 0.0 && t > 0.0) {
+      a = rr / t;
     }
-    __syncthreads();
-  } else if (threadIdx.x == 0) {
-    s_alpha = (float)A.sc->alpha;
+    if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; A.sc->rr_prev = rr; }
+    s_alpha = (float)a;
   }
-  if (!A.pq_part) __syncthreads();
+  __syncthreads();
   const float a = s_alpha;
   float acc = 0.f;
   while (i < A.n2) {
-    d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
-    r.x = fmaf(-a, q.x, r.x); r.y = fmaf(-a, q.y, r.y); r.z = fmaf(-a, q.z, r.z); r.w = fmaf(-a, q.w, r.w);
-    dx4[i] = d;
-    r4[i] = r;
-    acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
-    i += stride;
-    if (i < A.n2) { p = p4[i]; q = q4[i]; r = r4[i]; d = dx4[i]; }
+    cg_step_update(d0, r0, p0, q0, a, acc);
+    dx4[i] = d0;
+    r4[i] = r0;
+    const long i1 = i + stride;
+    if (i1 < A.n2) {
+      cg_step_update(d1, r1, p1, q1, a, acc);
+      dx4[i1] = d1;
+      r4[i1] = r1;
+    }
+    i += 2 * stride;
+    if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
+    if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
   }
-  __shared__ double red[32];
   const double s = nlv::block_sum((double)acc, red);
   if (threadIdx.x == 0) A.rr_part[bid] = s;
 }
