@@ -16,8 +16,27 @@
 namespace nlv {
 
 // ---------------------------------------------------------------------------------------------- complex ----
-__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums and differences on the GPU use the paired FP32 instructions (add/sub .f32x2, one instruction for
+// both parts, each part rounded as the scalar operation would be).
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "add.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+      : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+#else
+__host__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+#endif
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -32,6 +51,13 @@ __host__ __device__ __forceinline__ float2 mul_i(float2 a) { return make_float2(
 __host__ __device__ __forceinline__ float2 mul_mi(float2 a) { return make_float2(a.y, -a.x); }
 // exp(D i pi/2) * a for D = +-1
 template <int D> __host__ __device__ __forceinline__ float2 mul_di(float2 a) { return D > 0 ? mul_i(a) : mul_mi(a); }
+// a + D i b and a - D i b in scalar form: the swap and the sign of D i b fold into the two additions
+template <int D> __host__ __device__ __forceinline__ float2 cadd_di(float2 a, float2 b) {
+  return D > 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <int D> __host__ __device__ __forceinline__ float2 csub_di(float2 a, float2 b) {
+  return D > 0 ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
+}
 
 // ------------------------------------------------------------------------------ compile-time helpers ----
 template <class F, int... Is>
@@ -115,21 +141,22 @@ template <int D> struct RegDFT<3, D> {
     float2 s = cadd(a[1], a[2]);
     float2 d = csub(a[1], a[2]);
     float2 m = make_float2(fmaf(-0.5f, s.x, a[0].x), fmaf(-0.5f, s.y, a[0].y));
-    float2 r = cscale(mul_di<D>(d), h);                 // D i sin(2 pi/3) (a1 - a2)
+    // a1 = m + D i h d, a2 = m - D i h d, as fused multiply-adds
+    constexpr float dh = D > 0 ? h : -h;
     a[0] = cadd(a[0], s);
-    a[1] = cadd(m, r);
-    a[2] = csub(m, r);
+    a[1] = make_float2(fmaf(-dh, d.y, m.x), fmaf(dh, d.x, m.y));
+    a[2] = make_float2(fmaf(dh, d.y, m.x), fmaf(-dh, d.x, m.y));
   }
 };
 
 template <int D> struct RegDFT<4, D> {
   __host__ __device__ __forceinline__ static void run(float2* a) {
     float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
-    float2 s13 = cadd(a[1], a[3]), d13 = mul_di<D>(csub(a[1], a[3]));
+    float2 s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
     a[0] = cadd(s02, s13);
     a[2] = csub(s02, s13);
-    a[1] = cadd(d02, d13);
-    a[3] = csub(d02, d13);
+    a[1] = cadd_di<D>(d02, d13);
+    a[3] = csub_di<D>(d02, d13);
   }
 };
 
@@ -141,13 +168,13 @@ template <int D> struct RegDFT<5, D> {
     float2 b2 = cadd(a[2], a[3]), d2 = csub(a[2], a[3]);
     float2 e1 = make_float2(a[0].x + c1 * b1.x + c2 * b2.x, a[0].y + c1 * b1.y + c2 * b2.y);
     float2 e2 = make_float2(a[0].x + c2 * b1.x + c1 * b2.x, a[0].y + c2 * b1.y + c1 * b2.y);
-    float2 f1 = mul_di<D>(make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-    float2 f2 = mul_di<D>(make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    float2 f1 = make_float2(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+    float2 f2 = make_float2(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
     a[0] = make_float2(a[0].x + b1.x + b2.x, a[0].y + b1.y + b2.y);
-    a[1] = cadd(e1, f1);
-    a[4] = csub(e1, f1);
-    a[2] = cadd(e2, f2);
-    a[3] = csub(e2, f2);
+    a[1] = cadd_di<D>(e1, f1);
+    a[4] = csub_di<D>(e1, f1);
+    a[2] = cadd_di<D>(e2, f2);
+    a[3] = csub_di<D>(e2, f2);
   }
 };
 
