@@ -264,54 +264,75 @@ constexpr int kRowCtasPerSM = 2;
 
 // rho plane of the adjoint / normal / right-hand-side outputs: the sum of the channel products over the coils on
 // Omega (the channel summation of Table 1) plus the mode's alpha term.  Every block takes an equal slice of the
-// plane after its rows, all of its threads working on it; each thread issues its loads before its stores.
-template <int MODE>
+// plane after its rows, all of its threads working on it.  A thread takes two pixels per step (o and
+// o + blockDim.x) and issues every load of both before the first use; the coil sum of a pixel runs over even and
+// odd coils in two partial sums added at the end.
+template <int N, int MODE>
 __device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
-  const int N = A.N, f = A.f, Wc = A.Wc, J = A.J;
-  const long plane = (long)N * N;
+  const int f = A.f, Wc = A.Wc, J = A.J;
+  constexpr long plane = (long)N * N;
   const long e_begin = (long)bid * A.rho_per_cta;
   const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
   const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
+  const size_t stride = (size_t)Wc * Wc;
+  const long bd = blockDim.x;
   float acc = 0.f;
-  for (long o = e_begin + threadIdx.x; o < e_end; o += blockDim.x) {
-    const int e1 = (int)(o / N), e2 = (int)(o % N);
-    float2 z = make_float2(0.f, 0.f), a = z, b = z;
-    if constexpr (MODE == ROW_FFT_W_NORMAL) {
-      a = A.p[o];
-      if (A.pupd) b = A.r[o];
-    } else if constexpr (MODE == ROW_FFT_W_RHS) {
-      a = A.x[o];
-      b = A.xref[o];
-    }
-    if (in_omega(e1, N, f) && in_omega(e2, N, f)) {
-      const float2* zp = A.zsum + (size_t)to_compact(e1, N, f) * Wc + to_compact(e2, N, f);
-      const size_t stride = (size_t)Wc * Wc;
-      float2 z0 = z, z1 = z;
-      int j = 0;
-      for (; j + 2 <= J; j += 2) {
-        z0 = cadd(z0, zp[j * stride]);
-        z1 = cadd(z1, zp[(j + 1) * stride]);
+  for (long o0 = e_begin + threadIdx.x; o0 < e_end; o0 += 2 * bd) {
+    float2 a[2], b[2];
+    const float2* zp[2];
+    bool ok[2], om[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const long o = o0 + k * bd;
+      const int e1 = (int)(o / N), e2 = (int)(o % N);
+      ok[k] = o < e_end;
+      om[k] = ok[k] && in_omega(e1, N, f) && in_omega(e2, N, f);
+      zp[k] = A.zsum + (om[k] ? (size_t)to_compact(e1, N, f) * Wc + to_compact(e2, N, f) : 0);
+      a[k] = b[k] = make_float2(0.f, 0.f);
+      if (ok[k]) {
+        if constexpr (MODE == ROW_FFT_W_NORMAL) {
+          a[k] = A.p[o];
+          if (A.pupd) b[k] = A.r[o];
+        } else if constexpr (MODE == ROW_FFT_W_RHS) {
+          a[k] = A.x[o];
+          b[k] = A.xref[o];
+        }
       }
-      if (j < J) z0 = cadd(z0, zp[j * stride]);
-      z = cadd(z0, z1);
     }
-    if constexpr (MODE == ROW_FFT_W_ADJ) {
-      A.dst[o] = z;
-    } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
-      float2 pv = a;
-      if (A.pupd) {
-        pv = make_float2(fmaf(beta, pv.x, b.x), fmaf(beta, pv.y, b.y));
-        const_cast<float2*>(A.p)[o] = pv;
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 z00 = zero, z01 = zero, z10 = zero, z11 = zero;
+    int j = 0;
+    for (; j + 2 <= J; j += 2) {
+      if (om[0]) { z00 = cadd(z00, zp[0][j * stride]); z01 = cadd(z01, zp[0][(j + 1) * stride]); }
+      if (om[1]) { z10 = cadd(z10, zp[1][j * stride]); z11 = cadd(z11, zp[1][(j + 1) * stride]); }
+    }
+    if (j < J) {
+      if (om[0]) z00 = cadd(z00, zp[0][j * stride]);
+      if (om[1]) z10 = cadd(z10, zp[1][j * stride]);
+    }
+    const float2 z[2] = {cadd(z00, z01), cadd(z10, z11)};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!ok[k]) continue;
+      const long o = o0 + k * bd;
+      if constexpr (MODE == ROW_FFT_W_ADJ) {
+        A.dst[o] = z[k];
+      } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
+        float2 pv = a[k];
+        if (A.pupd) {
+          pv = make_float2(fmaf(beta, pv.x, b[k].x), fmaf(beta, pv.y, b[k].y));
+          const_cast<float2*>(A.p)[o] = pv;
+        }
+        const float2 q = make_float2(fmaf(A.alpha, pv.x, z[k].x), fmaf(A.alpha, pv.y, z[k].y));
+        A.dst[o] = q;
+        acc += pv.x * q.x + pv.y * q.y;
+      } else {
+        const float2 bb = make_float2(z[k].x - A.alpha * (a[k].x - b[k].x), z[k].y - A.alpha * (a[k].y - b[k].y));
+        A.r[o] = bb;
+        A.pout[o] = bb;
+        A.dx[o] = make_float2(0.f, 0.f);
+        acc += bb.x * bb.x + bb.y * bb.y;
       }
-      const float2 q = make_float2(fmaf(A.alpha, pv.x, z.x), fmaf(A.alpha, pv.y, z.y));
-      A.dst[o] = q;
-      acc += pv.x * q.x + pv.y * q.y;
-    } else {
-      const float2 bb = make_float2(z.x - A.alpha * (a.x - b.x), z.y - A.alpha * (a.y - b.y));
-      A.r[o] = bb;
-      A.pout[o] = bb;
-      A.dx[o] = make_float2(0.f, 0.f);
-      acc += bb.x * bb.x + bb.y * bb.y;
     }
   }
   return acc;
@@ -520,7 +541,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   __syncthreads();       // the next round restages the side rows
   }  // rounds
 
-  if constexpr (T::has_rho) acc += rho_slice<MODE>(A, bid);
+  if constexpr (T::has_rho) acc += rho_slice<N, MODE>(A, bid);
   if constexpr (T::reduces) {
     if (MODE == ROW_FFT_W_NORMAL && A.pq_only) {
       __shared__ double red[32];
