@@ -54,6 +54,12 @@ def test_realtime_frame_384(torch_cuda):
     _compare(torch_cuda, 384, 10, 13, 7, 30, seed=1003)
 
 
+def test_precision_frame_512(torch_cuda):
+    """512 x 512 grid, 16 coils, 32 spokes (the precision workload), on a shortened schedule so that the oracle
+    finishes in seconds: the final iterate and every Newton step's residual norm against the oracle."""
+    _compare(torch_cuda, 512, 16, 32, 2, 6, seed=1005)
+
+
 def test_graph_and_kernel_by_kernel_agree_bitwise(torch_cuda):
     torch = torch_cuda
     from paper_1301_1215_gb300.nlinv import Nlinv
