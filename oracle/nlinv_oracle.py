@@ -203,15 +203,60 @@ def irgnm(s: Setup, mask: np.ndarray, y: np.ndarray, x0: np.ndarray, xref: np.nd
     xr = x.copy() if xref is None else np.asarray(xref, dtype=np.complex128)
     norms = []
     for alpha in alpha_schedule(newton_steps, alpha0, q, alpha_min):
-        r0, nr = residual(s, mask, y, x)
+        x, nr = newton_step(s, mask, y, x, xr, alpha, cg_iters)
         norms.append(nr)
-        c = coils(s, x)
-        b = adjoint(s, mask, x, r0, c) - alpha * (x - xr)
-        xn = x
-        dx = cg(lambda d: normal(s, mask, xn, d, alpha, c), b, cg_iters)
-        x = x + dx
     norms.append(residual(s, mask, y, x)[1])
     return x, norms
+
+
+def newton_step(s: Setup, mask: np.ndarray, y: np.ndarray, x: np.ndarray, xr: np.ndarray, alpha: float,
+                cg_iters: int):
+    """One step of Eq. 3: b = DF^H(y - F x) - alpha (x - x_ref), (DF^H DF + alpha I) dx = b by CG, x + dx.
+    Returns the new iterate and |y - F x| at the old one."""
+    r0, nr = residual(s, mask, y, x)
+    c = coils(s, x)
+    b = adjoint(s, mask, x, r0, c) - alpha * (x - xr)
+    dx = cg(lambda d: normal(s, mask, x, d, alpha, c), b, cg_iters)
+    return x + dx, nr
+
+
+def irgnm_path(s: Setup, mask: np.ndarray, y: np.ndarray, x0: np.ndarray, xref: np.ndarray | None,
+               newton_steps: int, cg_iters: int, alpha0: float = 1.0, q: float = 0.5, alpha_min: float = 0.0):
+    """irgnm with every iterate kept: returns [x_0 .. x_N] and [alpha_0 .. alpha_{N-1}] (the checkpoints that the
+    gradient through the reconstruction needs)."""
+    xs = [np.array(x0, dtype=np.complex128, copy=True)]
+    xr = xs[0].copy() if xref is None else np.asarray(xref, dtype=np.complex128)
+    alphas = alpha_schedule(newton_steps, alpha0, q, alpha_min)
+    for alpha in alphas:
+        xs.append(newton_step(s, mask, y, xs[-1], xr, alpha, cg_iters)[0])
+    return xs, alphas
+
+
+def irgnm_vjp(s: Setup, mask: np.ndarray, y: np.ndarray, xs, alphas, g: np.ndarray, cg_iters: int):
+    """Gradient of a real loss L(x_N) through the Gauss-Newton iteration, from g = dL/dx_N, with every CG solve
+    taken as exact (implicit differentiation of each Newton step; exact when CG has converged).  Gradients are
+    with respect to the real inner product Re<u, v>: dL = Re<g, dx>.
+
+    With A = DF^H DF + alpha I at x = x_n, the step dx = x_{n+1} - x_n and s = y - F(x) - DF_x dx, the Jacobian
+    of x_{n+1} with respect to x_n is d -> A^-1 (DF_d^H s - DF_x^H DF_dx d), using that F is bilinear
+    (DF_x d = DF_d x and DF_{x+d} = DF_x + DF_d).  Per step, backwards: u = A^-1 g (CG),
+    dL/dy += DF_x u, dL/dx_ref += alpha u, and g <- DF_u^H s - DF_dx^H (DF_x u).
+    Returns (dL/dy, dL/dx_0, dL/dx_ref); when the iteration regularises toward x_0, dL/dx_0 is the sum of the
+    last two."""
+    gy = np.zeros_like(np.asarray(y, dtype=np.complex128))
+    gref = np.zeros_like(xs[0])
+    g = np.array(g, dtype=np.complex128, copy=True)
+    for k in reversed(range(len(alphas))):
+        x, alpha = xs[k], alphas[k]
+        dx = xs[k + 1] - x
+        c = coils(s, x)
+        u = cg(lambda d: normal(s, mask, x, d, alpha, c), g, cg_iters)
+        v = derivative(s, mask, x, u, c)
+        sres = y - forward(s, mask, x) - derivative(s, mask, x, dx, c)
+        gy = gy + v
+        gref = gref + alpha * u
+        g = adjoint(s, mask, u, sres) - adjoint(s, mask, dx, v)
+    return gy, g, gref
 
 
 def realtime_series(s: Setup, masks, ys, x0: np.ndarray, newton_steps: int, cg_iters: int,

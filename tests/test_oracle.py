@@ -375,3 +375,63 @@ def test_image_of_flat_coils_is_centred_rho():
     y[0] *= 2.0
     y[1:] /= 2.0
     assert rel(O.image(s, y), img) < 1e-13
+
+
+# ------------------------------------------------------------------------ gradient through the reconstruction ----
+
+def _vjp_problem(seed):
+    """8x8 grid, 2 coils: the CG solves of Eq. 3 converge to rounding in 250 iterations, so the implicit
+    gradient is the exact derivative of the iteration."""
+    s = O.Setup(8, 2, 2)
+    rng = synth.rng_for(seed)
+    mask = synth.radial_mask(8, 3)
+    x0 = synth.initial_guess(8, 2) + 0.1 * synth.random_complex((3, 8, 8), rng)
+    xref = synth.initial_guess(8, 2) + 0.1 * synth.random_complex((3, 8, 8), rng)
+    y = mask * synth.random_complex((2, 8, 8), rng)
+    g = synth.random_complex((3, 8, 8), rng)
+    return s, rng, mask, x0, xref, y, g
+
+
+def _loss(s, mask, y, x0, xref, g, newton=2, cg_iters=250):
+    x, _ = O.irgnm(s, mask, y, x0, xref, newton, cg_iters)
+    return O.inner(g, x).real
+
+
+@pytest.mark.parametrize("wrt", ["y", "x0", "xref"])
+def test_irgnm_vjp_matches_central_differences(wrt):
+    s, rng, mask, x0, xref, y, g = _vjp_problem(41)
+    xs, alphas = O.irgnm_path(s, mask, y, x0, xref, 2, 250)
+    assert np.allclose(xs[-1], O.irgnm(s, mask, y, x0, xref, 2, 250)[0], rtol=0, atol=1e-12)
+    gy, gx0, gref = O.irgnm_vjp(s, mask, y, xs, alphas, g, 250)
+    eps = 1e-6
+    if wrt == "y":
+        d = mask * synth.random_complex(y.shape, rng)
+        fd = (_loss(s, mask, y + eps * d, x0, xref, g) - _loss(s, mask, y - eps * d, x0, xref, g)) / (2 * eps)
+        grad = gy
+    elif wrt == "x0":
+        d = synth.random_complex(x0.shape, rng)
+        fd = (_loss(s, mask, y, x0 + eps * d, xref, g) - _loss(s, mask, y, x0 - eps * d, xref, g)) / (2 * eps)
+        grad = gx0
+    else:
+        d = synth.random_complex(xref.shape, rng)
+        fd = (_loss(s, mask, y, x0, xref + eps * d, g) - _loss(s, mask, y, x0, xref - eps * d, g)) / (2 * eps)
+        grad = gref
+    assert abs(O.inner(grad, d).real - fd) <= 1e-6 * abs(fd)
+
+
+def test_irgnm_vjp_with_start_as_reference_sums_both_paths():
+    """A single frame regularises toward its start value: x_ref = x_0 moves with x_0."""
+    s, rng, mask, x0, _, y, g = _vjp_problem(43)
+    xs, alphas = O.irgnm_path(s, mask, y, x0, None, 2, 250)
+    gy, gx0, gref = O.irgnm_vjp(s, mask, y, xs, alphas, g, 250)
+    d = synth.random_complex(x0.shape, rng)
+    eps = 1e-6
+    fd = (_loss(s, mask, y, x0 + eps * d, None, g) - _loss(s, mask, y, x0 - eps * d, None, g)) / (2 * eps)
+    assert abs(O.inner(gx0 + gref, d).real - fd) <= 1e-6 * abs(fd)
+
+
+def test_irgnm_vjp_ignores_data_outside_the_mask():
+    s, rng, mask, x0, xref, y, g = _vjp_problem(47)
+    xs, alphas = O.irgnm_path(s, mask, y, x0, xref, 2, 250)
+    gy = O.irgnm_vjp(s, mask, y, xs, alphas, g, 250)[0]
+    assert not gy[:, mask == 0].any()
