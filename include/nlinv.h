@@ -135,6 +135,35 @@ NLINV_API nlinv_status nlinv_simulate(nlinv_ctx* ctx, const nlinv_c32* rho, cons
 NLINV_API nlinv_status nlinv_reconstruct(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x_ref,
                                nlinv_c32* x_inout, double* resid);
 
+/* ------------------------------------------------------------------- gradient through the reconstruction ----
+ * The paper differentiates nothing; these two calls give the gradient of a real loss L(x_N) of the reconstruction
+ * with respect to its data, start value and regularisation centre, for training systems that put NLINV inside a
+ * larger model.  Every Gauss-Newton step of Eq. 3 is differentiated implicitly, its CG solve taken as exact (the
+ * gradient of the method when CG has converged).  With A = DF^H DF + alpha_n I at x_n, dx_n = x_{n+1} - x_n and
+ * s = y - F(x_n) - DF_{x_n} dx_n, one step backwards is: u = A^-1 g by the reconstruction's CG (params.cg_iters
+ * iterations); dL/dy += DF_{x_n} u; dL/dx_ref += alpha_n u; g <- DF_u^H s - DF_{dx_n}^H DF_{x_n} u (F is bilinear).
+ * Gradients are taken with respect to the real inner product Re sum conj(a) b (the convention of PyTorch's
+ * complex autograd).  All pointers are DEVICE pointers; every call is queued on the context's stream. */
+
+/* nlinv_reconstruct, plus the iterates x_0 .. x_N written to ckpt (DEVICE, (newton_steps+1) x (1+J) planes,
+ * owned by the caller): the per-Newton-step checkpoints of the gradient.  Launches the passes one by one (no graph).
+ * Waits for the stream only when resid (HOST, newton_steps+1 doubles) is given.  Errors: EINVAL (NULL or host
+ * pointers), ECUDA; EBREAKDOWN when the call waited and CG broke down. */
+NLINV_API nlinv_status nlinv_reconstruct_checkpoints(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask,
+                                                     const nlinv_c32* x_ref, nlinv_c32* x_inout, nlinv_c32* ckpt,
+                                                     double* resid);
+
+/* Backward pass from grad_x = dL/dx_N (1+J planes) over the checkpoints of nlinv_reconstruct_checkpoints with the
+ * same y and mask.  Writes grad_y (J planes, zero off the sampling pattern), grad_x0 (1+J planes) and, unless
+ * grad_xref is NULL, grad_xref (1+J planes).  tied = 1 when the reconstruction regularised toward its start value
+ * (x_ref NULL): grad_x0 then receives dL/dx_0 + dL/dx_ref, the gradient with respect to that start value.  The
+ * first call allocates 4 unknown-space vectors and 2 data arrays of scratch, held until nlinv_destroy.  The
+ * context's workspace (and so the state left for nlinv_profile_cg) is overwritten.  Errors: EINVAL, ENOMEM,
+ * ECUDA. */
+NLINV_API nlinv_status nlinv_reconstruct_vjp(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask,
+                                             const nlinv_c32* ckpt, const nlinv_c32* grad_x, int tied,
+                                             nlinv_c32* grad_y, nlinv_c32* grad_x0, nlinv_c32* grad_xref);
+
 /* ---------------------------------------------------------------------------------------------- batches ----
  * Many independent frames (slices, series of different patients, ...) of uneven grid side and coil count,
  * reconstructed together: every pass of Eq. 3 is one launch per grid side covering all frames of that side, and

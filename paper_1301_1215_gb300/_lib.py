@@ -43,6 +43,8 @@ SIGNATURES = {
     "nlinv_simulate": (_int, [_vp, _vp, _vp, _vp, _vp]),
     "nlinv_image": (_int, [_vp, _vp, _vp]),
     "nlinv_reconstruct": (_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "nlinv_reconstruct_checkpoints": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nlinv_reconstruct_vjp": (_int, [_vp, _vp, _vp, _vp, _vp, _int, _vp, _vp, _vp]),
     "nlinv_wait": (_int, [_vp, _dbl]),
     "nlinv_profile_cg": (_int, [_vp, _int, C.POINTER(_dbl)]),
     "nlinv_forward_noalloc": (_int, [C.POINTER(Params), _vp, _vp, _vp, _vp]),

@@ -78,6 +78,7 @@ struct KArgs {
   // iteration (its one consumer) adds the n_rr partials to form beta.  rr_part = NULL: beta from Scalars.
   double* rr_part;
   int n_rr;
+  float coef;               // vector passes: second coefficient of out = alpha X + coef Y
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----

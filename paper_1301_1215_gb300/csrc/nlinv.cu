@@ -127,6 +127,37 @@ __global__ void add_kernel(const KArgs A) {
   nlv::pdl_enter();
   add_body(A, blockIdx.x, gridDim.x);
 }
+// out = alpha X + coef Y (X = A.src, Y = A.q, out = A.dst) over A.n2 float4
+__global__ void axpby_kernel(const KArgs A) {
+  nlv::pdl_enter();
+  const float4* __restrict__ x4 = (const float4*)A.src;
+  const float4* __restrict__ y4 = (const float4*)A.q;
+  float4* __restrict__ o4 = (float4*)A.dst;
+  const float a = A.alpha, b = A.coef;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)gridDim.x * blockDim.x) {
+    const float4 x = x4[i], y = y4[i];
+    o4[i] = make_float4(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z), fmaf(a, x.w, b * y.w));
+  }
+}
+
+// CG from dx = 0 for the right-hand side b = A.src: r = p = b, dx = 0, |b|^2 -> RED_RR_INIT
+__global__ void cg_init_kernel(const KArgs A) {
+  nlv::pdl_enter();
+  const float4* __restrict__ b4 = (const float4*)A.src;
+  float4* __restrict__ r4 = (float4*)A.r;
+  float4* __restrict__ p4 = (float4*)A.pout;
+  float4* __restrict__ d4 = (float4*)A.dx;
+  float acc = 0.f;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)gridDim.x * blockDim.x) {
+    const float4 b = b4[i];
+    r4[i] = b;
+    p4[i] = b;
+    d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
+  }
+  nlv::grid_reduce(acc, A, blockIdx.x, gridDim.x);
+}
+
 __global__ void cg_step_batch(const nlv::BatchArgs B) {
   nlv::pdl_enter();
   int bid, nblk;
@@ -190,6 +221,8 @@ struct nlinv_ctx {
   std::vector<Rec>* rec = nullptr;   // non-null: launches are recorded instead of issued
   bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
+  float2* ckpt = nullptr;     // non-null: q_reconstruct writes x_0 .. x_N here (nlinv_reconstruct_checkpoints)
+  void* vjp_base = nullptr;   // scratch of nlinv_reconstruct_vjp (allocated on first use)
   std::string err;
 };
 
@@ -442,11 +475,55 @@ cudaError_t q_residual(nlinv_ctx* c, int slot) {
   return row(c, nlv::ROW_FFT_RESID, a);
 }
 
+// out = a X + b Y over one unknown-space vector ((1+J) planes) or, with planes = J, one data array.
+cudaError_t q_axpby(nlinv_ctx* c, float2* out, float a, const float2* X, float b, const float2* Y, long planes) {
+  KArgs k = base_args(c);
+  k.src = X;
+  k.q = Y;
+  k.dst = out;
+  k.alpha = a;
+  k.coef = b;
+  k.n2 = planes * c->plane / 2;
+  void* args[] = {&k};
+  return launch(c, (const void*)axpby_kernel, c->vec_blocks, kVecThreads, 0, args);
+}
+
+// out = DF_z d (J data planes) at the linearisation point z.
+cudaError_t q_derivative_to(nlinv_ctx* c, const float2* z, const float2* d, const uint8_t* mask, float2* out) {
+  cudaError_t e = q_coils(c, z);
+  if (e == cudaSuccess) e = q_dir(c, z, d);
+  if (e != cudaSuccess) return e;
+  KArgs a = base_args(c);
+  a.src = c->T;
+  a.dst = out;
+  a.mask = mask;
+  return row(c, nlv::ROW_FFT_P_OUT, a);
+}
+
+// out = DF_z^H r (one unknown-space vector) at the linearisation point z.
+cudaError_t q_adjoint_to(nlinv_ctx* c, const float2* z, const float2* r, const uint8_t* mask, float2* out) {
+  cudaError_t e = q_coils(c, z);
+  if (e != cudaSuccess) return e;
+  KArgs a = base_args(c);
+  a.src = r;
+  a.dst = c->T;
+  a.mask = mask;
+  if ((e = row(c, nlv::ROW_P_IFFT, a)) != cudaSuccess) return e;
+  if ((e = q_adj_col(c, z)) != cudaSuccess) return e;
+  a = base_args(c);
+  a.src = c->T;
+  a.dst = out;
+  a.zsum = c->zsum;
+  return row(c, nlv::ROW_FFT_W_ADJ, a);
+}
+
 // The whole reconstruction on the workspace buffers (x, xref, y, mask already in place).
 cudaError_t q_reconstruct(nlinv_ctx* c) {
   const nlinv_params& P = c->prm;
   double alpha = P.alpha0;
   cudaError_t e;
+  const size_t vb = c->vec * sizeof(float2);
+  if (c->ckpt && (e = cudaMemcpyAsync(c->ckpt, c->x, vb, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess) return e;
   for (int n = 0; n < P.newton_steps; ++n) {
     const float al = (float)alpha;
     if ((e = q_residual(c, n)) != cudaSuccess) return e;
@@ -471,6 +548,10 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     for (int i = 0; i < P.cg_iters; ++i)
       if ((e = q_cg_iter(c, c->x, al, i == 0)) != cudaSuccess) return e;
     if ((e = q_add(c)) != cudaSuccess) return e;
+    if (c->ckpt &&
+        (e = cudaMemcpyAsync(c->ckpt + (size_t)(n + 1) * c->vec, c->x, vb, cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess)
+      return e;
     c->last_alpha = alpha;
     alpha = std::max(alpha * P.alpha_q, P.alpha_min);
   }
@@ -700,6 +781,7 @@ nlinv_status nlinv_destroy(nlinv_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
   cudaFree(c->base);
+  if (c->vjp_base) cudaFree(c->vjp_base);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return NLINV_OK;
@@ -731,15 +813,7 @@ nlinv_status nlinv_derivative(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* m
       (s = check_dev(c, out, "out")))
     return s;
   c->launches = 0;
-  cudaError_t e = q_coils(c, (const float2*)x);
-  if (e == cudaSuccess) e = q_dir(c, (const float2*)x, (const float2*)dx);
-  if (e == cudaSuccess) {
-    KArgs a = base_args(c);
-    a.src = c->T;
-    a.dst = (float2*)out;
-    a.mask = mask;
-    e = row(c, nlv::ROW_FFT_P_OUT, a);
-  }
+  const cudaError_t e = q_derivative_to(c, (const float2*)x, (const float2*)dx, mask, (float2*)out);
   return finish_call(c, e, "nlinv_derivative");
 }
 
@@ -751,22 +825,7 @@ nlinv_status nlinv_adjoint(nlinv_ctx* c, const nlinv_c32* x, const uint8_t* mask
       (s = check_dev(c, out, "out")))
     return s;
   c->launches = 0;
-  cudaError_t e = q_coils(c, (const float2*)x);
-  if (e == cudaSuccess) {
-    KArgs a = base_args(c);
-    a.src = (const float2*)r;
-    a.dst = c->T;
-    a.mask = mask;
-    e = row(c, nlv::ROW_P_IFFT, a);
-  }
-  if (e == cudaSuccess) e = q_adj_col(c, (const float2*)x);
-  if (e == cudaSuccess) {
-    KArgs a = base_args(c);
-    a.src = c->T;
-    a.dst = (float2*)out;
-    a.zsum = c->zsum;
-    e = row(c, nlv::ROW_FFT_W_ADJ, a);
-  }
+  const cudaError_t e = q_adjoint_to(c, (const float2*)x, (const float2*)r, mask, (float2*)out);
   return finish_call(c, e, "nlinv_adjoint");
 }
 
@@ -920,6 +979,130 @@ nlinv_status nlinv_wait(nlinv_ctx* c, double timeout_s) {
     return fail(c, NLINV_EBREAKDOWN, "CG breakdown: a non-finite |r|^2 or Re<p, A p>");
   }
   return NLINV_OK;
+}
+
+nlinv_status nlinv_reconstruct_checkpoints(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask,
+                                           const nlinv_c32* x_ref, nlinv_c32* x_inout, nlinv_c32* ckpt,
+                                           double* resid) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, y, "y")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, x_inout, "x_inout")) ||
+      (s = check_dev(c, ckpt, "ckpt")))
+    return s;
+  if (x_ref && (s = check_dev(c, x_ref, "x_ref"))) return s;
+  const size_t vb = c->vec * sizeof(float2), db = (size_t)c->J * c->plane * sizeof(float2);
+  NLV_TRY(cudaMemcpyAsync(c->y, y, db, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+  NLV_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->plane, cudaMemcpyDeviceToDevice, c->stream), "copy mask");
+  NLV_TRY(cudaMemcpyAsync(c->x, x_inout, vb, cudaMemcpyDeviceToDevice, c->stream), "copy x");
+  NLV_TRY(cudaMemcpyAsync(c->xref, x_ref ? (const void*)x_ref : (const void*)c->x, vb, cudaMemcpyDeviceToDevice,
+                          c->stream), "copy x_ref");
+  c->launches = 0;
+  c->ckpt = (float2*)ckpt;
+  const cudaError_t e = q_reconstruct(c);
+  c->ckpt = nullptr;
+  NLV_TRY(e, "reconstruction");
+  c->have_state = true;
+  NLV_TRY(cudaMemcpyAsync(x_inout, c->x, vb, cudaMemcpyDeviceToDevice, c->stream), "copy x out");
+  if (resid) {
+    Scalars hs{};
+    NLV_TRY(cudaMemcpyAsync(&hs, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream), "read scalars");
+    NLV_TRY(cudaStreamSynchronize(c->stream), "synchronize");
+    for (int n = 0; n <= c->prm.newton_steps; ++n) resid[n] = hs.resid[n];
+    if (hs.flags & 1) {
+      int zero = 0;
+      cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(c, NLINV_EBREAKDOWN, "CG breakdown: a non-finite |r|^2 or Re<p, A p>");
+    }
+  }
+  return NLINV_OK;
+}
+
+nlinv_status nlinv_reconstruct_vjp(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* ckpt,
+                                   const nlinv_c32* grad_x, int tied, nlinv_c32* grad_y, nlinv_c32* grad_x0,
+                                   nlinv_c32* grad_xref) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status s;
+  if ((s = check_dev(c, y, "y")) || (s = check_dev(c, mask, "mask")) || (s = check_dev(c, ckpt, "ckpt")) ||
+      (s = check_dev(c, grad_x, "grad_x")) || (s = check_dev(c, grad_y, "grad_y")) ||
+      (s = check_dev(c, grad_x0, "grad_x0")))
+    return s;
+  if (grad_xref && (s = check_dev(c, grad_xref, "grad_xref"))) return s;
+  const nlinv_params& P = c->prm;
+  const long J = c->J, V = 1 + J;
+  const size_t vb = c->vec * sizeof(float2), db = (size_t)J * c->plane * sizeof(float2);
+  if (!c->vjp_base) {   // g, dx_n, one adjoint result, dL/dx_ref; s and DF_x u (data arrays)
+    cudaError_t e = cudaMalloc(&c->vjp_base, 4 * vb + 2 * db);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->vjp_base = nullptr;
+      return fail(c, NLINV_ENOMEM, "nlinv_reconstruct_vjp: scratch allocation failed");
+    }
+  }
+  float2* g = (float2*)c->vjp_base;
+  float2* dxn = g + c->vec;
+  float2* tmp = dxn + c->vec;
+  float2* gref = tmp + c->vec;
+  float2* sres = gref + c->vec;
+  float2* v = sres + J * c->plane;
+  const float2* X = (const float2*)ckpt;
+  c->launches = 0;
+  NLV_TRY(cudaMemcpyAsync(c->y, y, db, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+  NLV_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->plane, cudaMemcpyDeviceToDevice, c->stream), "copy mask");
+  NLV_TRY(cudaMemcpyAsync(g, grad_x, vb, cudaMemcpyDeviceToDevice, c->stream), "copy grad_x");
+  NLV_TRY(cudaMemsetAsync(grad_y, 0, db, c->stream), "clear grad_y");
+  NLV_TRY(cudaMemsetAsync(gref, 0, vb, c->stream), "clear dL/dx_ref");
+  std::vector<double> alphas(P.newton_steps);
+  double al = P.alpha0;
+  for (int n = 0; n < P.newton_steps; ++n) {
+    alphas[n] = al;
+    al = std::max(al * P.alpha_q, P.alpha_min);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = P.newton_steps - 1; k >= 0 && e == cudaSuccess; --k) {
+    const float alpha = (float)alphas[k];
+    const float2* xk = X + (size_t)k * c->vec;
+    e = cudaMemcpyAsync(c->x, xk, vb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = q_axpby(c, dxn, 1.f, xk + c->vec, -1.f, xk, V);
+    // r0 = y - F x_k, then s = r0 - DF_x dx_k (both as "data minus masked transform" row passes)
+    if (e == cudaSuccess) e = q_coils(c, c->x);
+    if (e == cudaSuccess) e = q_prod(c, c->x);
+    if (e == cudaSuccess) {
+      KArgs a = base_args(c);
+      a.src = c->T; a.dst = c->r0; a.y = c->y; a.mask = c->mask;
+      e = row(c, nlv::ROW_FFT_RESID, a);
+    }
+    if (e == cudaSuccess) e = q_dir(c, c->x, dxn);
+    if (e == cudaSuccess) {
+      KArgs a = base_args(c);
+      a.src = c->T; a.dst = sres; a.y = c->r0; a.mask = c->mask;
+      e = row(c, nlv::ROW_FFT_RESID, a);
+    }
+    // u = (DF^H DF + alpha)^-1 g by the reconstruction's CG (u in c->dx)
+    if (e == cudaSuccess) {
+      KArgs a = base_args(c);
+      a.src = g; a.r = c->r; a.pout = c->p; a.dx = c->dx; a.n2 = c->vec / 2; a.reduce = nlv::RED_RR_INIT;
+      void* args[] = {&a};
+      e = launch(c, (const void*)cg_init_kernel, c->vec_blocks, kVecThreads, 0, args);
+    }
+    for (int i = 0; i < P.cg_iters && e == cudaSuccess; ++i) e = q_cg_iter(c, c->x, alpha, i == 0);
+    // v = DF_x u; dL/dy += v; dL/dx_ref += alpha u
+    if (e == cudaSuccess) e = q_dir(c, c->x, c->dx);
+    if (e == cudaSuccess) {
+      KArgs a = base_args(c);
+      a.src = c->T; a.dst = v; a.mask = c->mask;
+      e = row(c, nlv::ROW_FFT_P_OUT, a);
+    }
+    if (e == cudaSuccess) e = q_axpby(c, (float2*)grad_y, 1.f, (const float2*)grad_y, 1.f, v, J);
+    if (e == cudaSuccess) e = q_axpby(c, gref, 1.f, gref, alpha, c->dx, V);
+    // g <- DF_u^H s - DF_dx^H v
+    if (e == cudaSuccess) e = q_adjoint_to(c, c->dx, sres, c->mask, tmp);
+    if (e == cudaSuccess) e = q_adjoint_to(c, dxn, v, c->mask, g);
+    if (e == cudaSuccess) e = q_axpby(c, g, 1.f, tmp, -1.f, g, V);
+  }
+  // dL/dx_0 (plus dL/dx_ref when the reference is the start value)
+  if (e == cudaSuccess) e = q_axpby(c, (float2*)grad_x0, 1.f, g, tied ? 1.f : 0.f, gref, V);
+  if (e == cudaSuccess && grad_xref) e = cudaMemcpyAsync(grad_xref, gref, vb, cudaMemcpyDeviceToDevice, c->stream);
+  return finish_call(c, e, "nlinv_reconstruct_vjp");
 }
 
 nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {

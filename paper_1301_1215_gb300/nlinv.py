@@ -192,6 +192,41 @@ class Nlinv:
         are copied through the library's workspace (the call then waits for the result)."""
         return self._run(y, mask, x_ref, x_inout, resid)
 
+    def reconstruct_checkpoints(self, y: torch.Tensor, mask: torch.Tensor, x0: Optional[torch.Tensor] = None,
+                                x_ref: Optional[torch.Tensor] = None):
+        """Reconstruction that also keeps every Gauss-Newton iterate (nlinv_reconstruct_checkpoints).  Returns
+        (x_N, checkpoints) with checkpoints of shape (newton_steps + 1, 1+J, n, n): x_0 .. x_N."""
+        y, mask = self._y(y), self._m(mask)
+        if x0 is None:
+            x = torch.zeros(self._shape_x(), dtype=torch.complex64, device=self.device)
+            x[0] = 1.0
+        else:
+            x = self._x(x0, "x0").clone()
+        xr = None if x_ref is None else self._x(x_ref, "x_ref")
+        ck = torch.empty((self.params.newton_steps + 1,) + self._shape_x(), dtype=torch.complex64, device=self.device)
+        self._begin()
+        self._check(self._lib.nlinv_reconstruct_checkpoints(self._h, _ptr(y), _ptr(mask), _ptr(xr), _ptr(x),
+                                                            _ptr(ck), None))
+        self._end()
+        return x, ck
+
+    def reconstruct_vjp(self, y: torch.Tensor, mask: torch.Tensor, checkpoints: torch.Tensor,
+                        grad_x: torch.Tensor, want_xref: bool = True, tied: bool = False):
+        """Backward pass of the reconstruction (nlinv_reconstruct_vjp) from dL/dx_N over ``checkpoints``.
+        Returns (dL/dy, dL/dx_0, dL/dx_ref or None); with ``tied`` (the reconstruction regularised toward its start
+        value) the second entry is the gradient with respect to that start value."""
+        y, mask, gx = self._y(y), self._m(mask), self._x(grad_x, "grad_x")
+        ck = self._dev(checkpoints, (self.params.newton_steps + 1,) + self._shape_x(), torch.complex64,
+                       "checkpoints")
+        gy = torch.empty(self._shape_y(), dtype=torch.complex64, device=self.device)
+        g0 = torch.empty(self._shape_x(), dtype=torch.complex64, device=self.device)
+        gr = torch.empty(self._shape_x(), dtype=torch.complex64, device=self.device) if want_xref else None
+        self._begin()
+        self._check(self._lib.nlinv_reconstruct_vjp(self._h, _ptr(y), _ptr(mask), _ptr(ck), _ptr(gx),
+                                                    1 if tied else 0, _ptr(gy), _ptr(g0), _ptr(gr)))
+        self._end()
+        return gy, g0, gr
+
     def _run(self, y, mask, xr, x, resid):
         nres = self.params.newton_steps + 1
         buf = (C.c_double * nres)() if resid else None
