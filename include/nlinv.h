@@ -206,9 +206,11 @@ NLINV_API nlinv_status nlinv_batch_destroy(nlinv_batch* batch);
  * error. */
 NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
 
-/* Times the kernels of one CG iteration of Eq. 3 with CUDA events on the context's stream, launching them one by
- * one reps times on the workspace left by the last nlinv_reconstruct (whose CG state it advances; x is not
- * changed).  ms_out (HOST, 6 doubles) receives the mean duration in milliseconds of, in order:
+/* Times the kernels of one CG iteration of Eq. 3 with CUDA events on the context's stream, on the workspace left
+ * by the last nlinv_reconstruct (whose CG state it advances; x is not changed): each kernel is launched reps times
+ * back to back between two events, so ms_out gets its steady-state launch duration (consecutive launches overlap
+ * their ramp and drain, as the passes of a graph replay do).  With reps = 1 the six kernels run once each, in
+ * order.  ms_out (HOST, 6 doubles) receives the mean duration in milliseconds of, in order:
  *   [0] row pass  p = r + beta p, W^-1 (first axis)   [1] column pass  W^-1, C (products), FFT
  *   [2] row pass  PSF                                  [3] column pass  FFT^-1, C^H (channel products), FFT
  *   [4] row pass  W^-H + alpha p, Re<p, q>             [5] CG step  dx += alpha p, r -= alpha q, |r|^2

@@ -1110,37 +1110,33 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   if (reps < 1 || !ms_out) return fail(c, NLINV_EINVAL, "reps must be >= 1 and ms_out non-NULL");
   if (!c->have_state) return fail(c, NLINV_EINVAL, "run nlinv_reconstruct before nlinv_profile_cg");
   constexpr int K = kProfileKernels;
-  cudaEvent_t ev[K + 1];
-  for (int i = 0; i <= K; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
-  double acc[K] = {0};
+  cudaEvent_t ev[2];
+  for (int i = 0; i < 2; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
   const float al = (float)c->last_alpha;
-  cudaError_t e = cudaSuccess;
-  for (int it = 0; it < reps && e == cudaSuccess; ++it) {
-    int k = 0;
-    auto mark = [&]() { if (e == cudaSuccess) e = cudaEventRecord(ev[k++], c->stream); };
-    mark();
-    if (e == cudaSuccess) e = q_cg_k1(c, false);
-    mark();
-    if (e == cudaSuccess) e = q_cg_k2(c, c->x);
-    mark();
-    if (e == cudaSuccess) e = q_cg_k3(c);
-    mark();
-    if (e == cudaSuccess) e = q_adj_col(c, c->x);
-    mark();
-    if (e == cudaSuccess) e = q_cg_k5(c, al);
-    mark();
-    if (e == cudaSuccess) e = q_cg_step(c, row_geom(c, true).blocks);
-    mark();
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[K]);
-    for (int i = 0; i < K && e == cudaSuccess; ++i) {
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-      acc[i] += ms;
+  // kernel k of the CG iteration, reps launches back to back between two events: its steady-state launch
+  // duration (consecutive launches overlap ramp and drain through the dependent launch, as in a graph replay)
+  auto one = [&](int k) -> cudaError_t {
+    switch (k) {
+      case 0: return q_cg_k1(c, false);
+      case 1: return q_cg_k2(c, c->x);
+      case 2: return q_cg_k3(c);
+      case 3: return q_adj_col(c, c->x);
+      case 4: return q_cg_k5(c, al);
+      default: return q_cg_step(c, row_geom(c, true).blocks);
     }
+  };
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(ev[0], c->stream);
+    for (int it = 0; it < reps && e == cudaSuccess; ++it) e = one(k);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ms_out[k] = ms / reps;
   }
-  for (int i = 0; i <= K; ++i) cudaEventDestroy(ev[i]);
+  for (int i = 0; i < 2; ++i) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return cuda_fail(c, e, "nlinv_profile_cg");
-  for (int i = 0; i < K; ++i) ms_out[i] = acc[i] / reps;
   return NLINV_OK;
 }
 
