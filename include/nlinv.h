@@ -217,6 +217,27 @@ NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
  * Waits for the stream.  Errors: EINVAL (reps < 1, NULL pointers, no reconstruction yet), ECUDA. */
 NLINV_API nlinv_status nlinv_profile_cg(nlinv_ctx* ctx, int reps, double* ms_out);
 
+/* Launch shapes picked by nlinv_autotune. */
+typedef struct {
+  int vec_blocks_per_sm;  /* blocks per SM of the vector passes (CG step, x update): 2, 4 or 8 */
+  int pdl;                /* 1: passes use programmatic dependent launch */
+  double ms_per_frame;    /* the measured time of one whole reconstruction with these shapes */
+} nlinv_tuning;
+
+/* Autotuner of the launch shapes (not part of the paper's method): reconstructs the caller's representative frame
+ * (y, mask, start value x0; DEVICE pointers, as for nlinv_reconstruct) as graph replays for every candidate
+ * (vector-pass blocks per SM x dependent launch on/off), reps timed replays each, every one from a cold L2 (a
+ * temporary buffer of twice the L2 size is written before it, outside the timing), and keeps the fastest for the
+ * context when it beats the compiled default (4 blocks per SM, dependent launch on unless NLINV_PDL=0) by 3 % or
+ * more; closer shapes swap places with small changes of conditions, so the default stays.  Whole frames of real data are timed: the passes overlap their neighbours inside a graph, so a pass timed
+ * alone can rank shapes wrongly, and an all-zero workspace times differently from data.  The workspace is
+ * overwritten.  The choice is cached per (device, n, ncoils, fov, newton_steps, cg_iters) for the process, so a
+ * second context of the same shape takes it without timing.  out (HOST) receives the choice and table (HOST,
+ * table_len >= 6 entries) every candidate's time, in the order pdl off then on, 2, 4, 8 blocks per SM; either may
+ * be NULL.  Errors: EINVAL (NULL or host pointers, reps outside 1..1000, a short table, a batch frame), ECUDA. */
+NLINV_API nlinv_status nlinv_autotune(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x0,
+                                      int reps, nlinv_tuning* out, nlinv_tuning* table, int table_len);
+
 /* Kernel launches queued by the last nlinv_reconstruct, nlinv_forward, ... call (the graph's kernel nodes when a
  * graph was replayed).  -1 for a NULL context. */
 NLINV_API long nlinv_last_launch_count(const nlinv_ctx* ctx);

@@ -25,6 +25,10 @@ class Params(C.Structure):
                 ("sobolev_a", _dbl), ("sobolev_l", _dbl), ("fov", _int), ("use_graph", _int)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("vec_blocks_per_sm", _int), ("pdl", _int), ("ms_per_frame", _dbl)]
+
+
 class FrameDesc(C.Structure):
     """Mirror of nlinv_frame_desc."""
     _fields_ = [("n", _int), ("ncoils", _int), ("y", _vp), ("mask", _vp), ("x_ref", _vp), ("x_inout", _vp),
@@ -53,6 +57,7 @@ SIGNATURES = {
     "nlinv_batch_launch_count": (_long, [_vp]),
     "nlinv_batch_destroy": (_int, [_vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
+    "nlinv_autotune": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(Tuning), C.POINTER(Tuning), _int]),
     "nlinv_last_error": (C.c_char_p, [_vp]),
 }
 

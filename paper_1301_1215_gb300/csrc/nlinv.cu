@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -172,6 +173,9 @@ __global__ void add_batch(const nlv::BatchArgs B) {
 }
 
 constexpr int kVecThreads = 256;
+constexpr int kTuneVecMax = 8;       // largest vector-kernel blocks per SM that nlinv_autotune tries
+constexpr int kTuneCandidates = 6;   // its candidates: {2, 4, 8} blocks per SM x dependent launch off / on
+constexpr double kTuneMargin = 0.03; // a candidate replaces the compiled default only when this much faster
 #ifndef NLV_VEC_BLOCKS_PER_SM
 #define NLV_VEC_BLOCKS_PER_SM 4   // blocks per SM of the vector passes
 #endif
@@ -698,7 +702,8 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   const size_t twb = align_up((size_t)c->N * cplx, 256);
   const size_t wb = align_up((size_t)c->plane * sizeof(float), 256);
   const size_t maskb = align_up((size_t)c->plane, 256);
-  const int max_blocks = std::max(row_geom(c, true).blocks, c->vec_blocks);
+  // partials sized for the largest vector grid that nlinv_autotune tries
+  const int max_blocks = std::max(row_geom(c, true).blocks, std::max(c->vec_blocks, c->sms * kTuneVecMax));
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
   const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 3 * partb + scb;
@@ -1141,6 +1146,121 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
 }
 
 long nlinv_last_launch_count(const nlinv_ctx* c) { return c ? c->launches : -1; }
+
+nlinv_status nlinv_autotune(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x0, int reps,
+                            nlinv_tuning* out, nlinv_tuning* table, int table_len) {
+  if (!c) return NLINV_EINVAL;
+  nlinv_status st;
+  if ((st = check_dev(c, y, "y")) || (st = check_dev(c, mask, "mask")) || (st = check_dev(c, x0, "x0"))) return st;
+  if (reps < 1 || reps > 1000) return fail(c, NLINV_EINVAL, "reps must be in 1..1000");
+  if (c->batch_lanes > 0) return fail(c, NLINV_EINVAL, "batch frames are not tuned one by one");
+  if (table && table_len < kTuneCandidates) return fail(c, NLINV_EINVAL, "table needs 6 entries");
+  struct Key { int dev, n, J, fov, newton, cg; };
+  struct Entry { Key k; nlinv_tuning t; nlinv_tuning all[kTuneCandidates]; };
+  static std::mutex mtx;
+  static std::vector<Entry> cache;
+  const Key key{c->device, c->N, c->J, c->f, c->prm.newton_steps, c->prm.cg_iters};
+  auto same = [&](const Key& a) {
+    return a.dev == key.dev && a.n == key.n && a.J == key.J && a.fov == key.fov && a.newton == key.newton &&
+           a.cg == key.cg;
+  };
+  auto apply = [&](const nlinv_tuning& t) {
+    c->vec_blocks = c->sms * t.vec_blocks_per_sm;
+    c->pdl = t.pdl != 0;
+    if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  };
+  {
+    std::lock_guard<std::mutex> lk(mtx);
+    for (const Entry& e : cache)
+      if (same(e.k)) {
+        apply(e.t);
+        if (out) *out = e.t;
+        if (table) std::copy(e.all, e.all + kTuneCandidates, table);
+        return NLINV_OK;
+      }
+  }
+  // Whole reconstructions of the caller's frame, replayed as graphs (each replay starts from the last result, as
+  // in a series): only the whole graph shows how neighbouring passes overlap, and an all-zero workspace times
+  // differently from data.
+  const size_t vb = c->vec * sizeof(float2), db = (size_t)c->J * c->plane * sizeof(float2);
+  NLV_TRY(cudaMemcpyAsync(c->y, y, db, cudaMemcpyDeviceToDevice, c->stream), "copy y");
+  NLV_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->plane, cudaMemcpyDeviceToDevice, c->stream), "copy mask");
+  // every timed replay starts with a cold L2 (a write of twice its size outside the events), as a frame of a
+  // series does after the rest of an application has run
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
+  const size_t flush_bytes = std::max<size_t>(2 * (size_t)l2, 64u << 20);
+  void* flush = nullptr;
+  if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, NLINV_ENOMEM, "nlinv_autotune: L2 flush buffer allocation failed");
+  }
+  cudaEvent_t ev[2];
+  for (int i = 0; i < 2; ++i) {
+    cudaError_t ee = cudaEventCreate(&ev[i]);
+    if (ee != cudaSuccess) { cudaFree(flush); return cuda_fail(c, ee, "event create"); }
+  }
+  const int vbs[] = {2, 4, kTuneVecMax};
+  nlinv_tuning best{};
+  best.ms_per_frame = 1e30;
+  nlinv_tuning dflt{NLV_VEC_BLOCKS_PER_SM, c->pdl ? 1 : 0, 0.0};   // the compiled default (and the PDL setting)
+  Entry ent{};
+  int ncand = 0;
+  cudaError_t e = cudaSuccess;
+  for (int pdl = 0; pdl < 2 && e == cudaSuccess; ++pdl)
+    for (int vbk : vbs) {
+      if (e != cudaSuccess) break;
+      nlinv_tuning t{vbk, pdl, 0.0};
+      apply(t);
+      e = cudaMemcpyAsync(c->x, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(c->xref, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
+      if (e != cudaSuccess) break;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) break;
+      cudaError_t e1 = q_reconstruct(c);
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+      e = e1 != cudaSuccess ? e1 : e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);                 // warm-up
+      double tot = 0.0;
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaMemsetAsync(flush, r & 0xff, flush_bytes, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        tot += ms;
+      }
+      if (ge) cudaGraphExecDestroy(ge);
+      t.ms_per_frame = tot / reps;
+      if (e == cudaSuccess) ent.all[ncand++] = t;
+      if (e == cudaSuccess && t.ms_per_frame < best.ms_per_frame) best = t;
+      if (e == cudaSuccess && t.vec_blocks_per_sm == dflt.vec_blocks_per_sm && t.pdl == dflt.pdl) dflt = t;
+    }
+  for (int i = 0; i < 2; ++i) cudaEventDestroy(ev[i]);
+  cudaFree(flush);
+  int zero = 0;   // the timing runs are not the caller's results: drop any flag they raised
+  if (e == cudaSuccess) e = cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "nlinv_autotune");
+  // Shapes within a few per cent swap places with small changes of conditions (other work between frames, the
+  // frame's own copies); the default stays unless a candidate beats it clearly.
+  if (dflt.ms_per_frame > 0.0 && best.ms_per_frame > (1.0 - kTuneMargin) * dflt.ms_per_frame) best = dflt;
+  apply(best);
+  ent.k = key;
+  ent.t = best;
+  {
+    std::lock_guard<std::mutex> lk(mtx);
+    cache.push_back(ent);
+  }
+  if (out) *out = best;
+  if (table) std::copy(ent.all, ent.all + kTuneCandidates, table);
+  return NLINV_OK;
+}
 
 }  // extern "C"
 

@@ -254,6 +254,28 @@ class Nlinv:
         self._end()
         return dict(zip(self.CG_KERNELS, [float(v) for v in ms]))
 
+    def autotune(self, y: torch.Tensor, mask: torch.Tensor, x0: Optional[torch.Tensor] = None,
+                 reps: int = 3) -> dict:
+        """Picks the launch shapes by timing whole graph-replayed reconstructions of a representative frame
+        (nlinv_autotune; x0 default: rho = 1, chat = 0); overwrites the workspace.  Returns the choice
+        (vector-pass blocks per SM, dependent launch on/off, ms per frame; the compiled default unless a candidate
+        is 3 % faster) and every candidate's time."""
+        y, mask = self._y(y), self._m(mask)
+        if x0 is None:
+            x0 = torch.zeros(self._shape_x(), dtype=torch.complex64, device=self.device)
+            x0[0] = 1.0
+        x0 = self._x(x0, "x0")
+        t = _lib.Tuning()
+        table = (_lib.Tuning * 6)()
+        self._begin()
+        self._check(self._lib.nlinv_autotune(self._h, _ptr(y), _ptr(mask), _ptr(x0), int(reps), C.byref(t),
+                                             table, 6))
+        self._end()
+        return {"vec_blocks_per_sm": int(t.vec_blocks_per_sm), "pdl": bool(t.pdl),
+                "ms_per_frame": float(t.ms_per_frame),
+                "candidates": [(int(e.vec_blocks_per_sm), bool(e.pdl), round(float(e.ms_per_frame), 4))
+                               for e in table]}
+
     @property
     def last_launch_count(self) -> int:
         """Kernel launches queued by the last call (kernel nodes of the graph when one was replayed)."""

@@ -60,6 +60,30 @@ def test_precision_frame_512(torch_cuda):
     _compare(torch_cuda, 512, 16, 32, 2, 6, seed=1005)
 
 
+def test_autotune_picks_a_candidate_and_keeps_parity(torch_cuda):
+    """The launch-shape autotuner times whole graph replays, keeps one of its candidates, and the reconstruction
+    with the chosen shapes still matches the oracle; a second context of the same shape takes the cached choice."""
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J = 64, 4
+    s, fr, y = noisy_data(n, J, 16, 1001)
+    y = y.astype(np.complex64).astype(np.complex128)
+    x0 = synth.initial_guess(n, J)
+    ty, tm, tx = _t(torch, y), _t(torch, fr.mask), _t(torch, x0)
+    with Nlinv(n, J, newton_steps=7, cg_iters=30) as ctx:
+        t = ctx.autotune(ty, tm, tx, reps=2)
+        assert t["vec_blocks_per_sm"] in (2, 4, 8) and t["ms_per_frame"] > 0
+        times = {(v, p): m for v, p, m in t["candidates"]}
+        assert times[(t["vec_blocks_per_sm"], t["pdl"])] == round(t["ms_per_frame"], 4)
+        if (t["vec_blocks_per_sm"], t["pdl"]) != (4, True):       # moved off the default only for a clear win
+            assert t["ms_per_frame"] <= 0.97 * times[(4, True)]
+        xg = ctx.reconstruct(ty, tm, tx).cpu().numpy()
+    xo, _ = O.irgnm(s, fr.mask, y, x0, None, 7, 30)
+    assert rel(xg, xo) < TOL_X
+    with Nlinv(n, J, newton_steps=7, cg_iters=30) as ctx:
+        assert ctx.autotune(ty, tm, tx, reps=2) == t
+
+
 def test_graph_and_kernel_by_kernel_agree_bitwise(torch_cuda):
     torch = torch_cuda
     from paper_1301_1215_gb300.nlinv import Nlinv
