@@ -761,12 +761,22 @@ struct BatchArgs {
 __device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int& bid, int& nblk) {
   __shared__ KArgs sa;
   __shared__ int sf, sb, sn;
-  if (threadIdx.x == 0) {
+  // the frame is the number of block offsets first[1 .. nframes-1] at or below this block (offsets increase):
+  // the first warp tests 32 of them per step, all loads of a step in flight together
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, nl = warp_lanes();
+    const unsigned live = nl >= 32 ? 0xffffffffu : (1u << nl) - 1u;
     int f = 0;
-    while (f + 1 < B.nframes && B.first[f + 1] <= (int)blockIdx.x) ++f;
-    sf = f;
-    sb = (int)blockIdx.x - B.first[f];
-    sn = B.first[f + 1] - B.first[f];
+    for (int base = 1; base < B.nframes; base += nl) {
+      const int k = base + lane;
+      const bool le = lane < nl && k < B.nframes && B.first[k] <= (int)blockIdx.x;
+      f += __popc(__ballot_sync(live, le));
+    }
+    if (lane == 0) {
+      sf = f;
+      sb = (int)blockIdx.x - B.first[f];
+      sn = B.first[f + 1] - B.first[f];
+    }
   }
   __syncthreads();
   const int* src = (const int*)(B.args + sf);
