@@ -20,7 +20,6 @@ enum Reduce : int {
   RED_NONE = 0,       // the block partials are summed into Scalars::last
   RED_RESID = 1,      // Scalars::resid[slot] = sqrt(sum)       (|y - F x_n|)
   RED_RR_INIT = 2,    // Scalars::rr = sum                      (|b|^2 at the start of CG)
-  RED_PQ = 3,         // Scalars::alpha = rr / sum              (sum = Re<p, A p>)
 };
 
 constexpr int kMaxNewton = 64;
@@ -69,11 +68,10 @@ struct KArgs {
   int slot;                 // RED_RESID index
   const float2* q;          // CG step: A p
   long n2;                  // vector passes: number of float4 (two complex values each)
-  // Re<p, A p> without a last-block tail: the normal-operator pass only writes one FP64 partial per block into
-  // pq_part (pq_only = 1); the CG step, its one consumer, adds the n_pq partials itself to form alpha.
+  // Re<p, A p> without a last-block tail: the normal-operator pass of the CG iteration only writes one FP64
+  // partial per block into pq_part; the CG step, its one consumer, adds the n_pq partials itself to form alpha.
   double* pq_part;
   int n_pq;
-  int pq_only;
   // |r|^2 likewise: the CG step writes one partial per block into rr_part, and the first pass of the next CG
   // iteration (its one consumer) adds the n_rr partials to form beta.  rr_part = NULL: beta from Scalars.
   double* rr_part;
@@ -149,16 +147,6 @@ __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slo
   switch (reduce) {
     case RED_RESID: sc->resid[slot] = sqrt(total); break;
     case RED_RR_INIT: sc->rr = total; sc->beta = 0.0; break;
-    case RED_PQ: {
-      // The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 (or |r|^2 = 0) only occurs once CG has
-      // reached the rounding floor: the step is then empty.  Non-finite values are a breakdown.
-      double rr = sc->rr, a = 0.0;
-      sc->pq = total;
-      if (!isfinite(total) || !isfinite(rr)) sc->flags |= 1;
-      else if (rr != 0.0 && total > 0.0) a = rr / total;
-      sc->alpha = a;
-      break;
-    }
     default: sc->last = total; break;
   }
 }
@@ -544,7 +532,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 
   if constexpr (T::has_rho) acc += rho_slice<N, MODE>(A, bid);
   if constexpr (T::reduces) {
-    if (MODE == ROW_FFT_W_NORMAL && A.pq_only) {
+    if (MODE == ROW_FFT_W_NORMAL && A.pq_part) {
       __shared__ double red[32];
       const double sblk = block_sum((double)acc, red);
       if (threadIdx.x == 0) A.pq_part[bid] = sblk;

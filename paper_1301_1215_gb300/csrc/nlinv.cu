@@ -48,7 +48,8 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
   float4* __restrict__ dx4 = (float4*)A.dx;
   // Two groups of operands per thread in flight: the first two are loaded while the block forms
   // alpha = |r|^2 / Re<p, A p> from the partials of the normal-operator pass (every block sums them in the same
-  // fixed order; empty step at the rounding floor, flag on non-finite values).
+  // fixed order).  The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 or |r|^2 = 0 only occurs once CG
+  // has reached the rounding floor: the step is then empty (alpha = 0).  Non-finite values set the breakdown flag.
   const long stride = (long)nblk * blockDim.x;
   long i = bid * (long)blockDim.x + threadIdx.x;
   float4 p0, q0, r0, d0, p1, q1, r1, d1;
@@ -448,8 +449,6 @@ cudaError_t q_cg_k5(nlinv_ctx* c, float alpha) {
   a.pupd = 1;
   a.zsum = c->zsum;
   a.alpha = alpha;
-  a.reduce = nlv::RED_PQ;
-  a.pq_only = 1;
   a.pq_part = c->pq_part;
   return row(c, nlv::ROW_FFT_W_NORMAL, a);
 }
