@@ -36,6 +36,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the compiled launch shapes (profiling runs: the tuner replays ~30k launches)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch64"],
                     help="realtime_384 (default): the real-time series; batch64: 64 independent frames of uneven "
                          "grid side and coil count, batched against plain per-frame reconstruction")
@@ -201,7 +203,10 @@ def run_ours(args, rank, world, local):
     ctx = Nlinv(W.n, W.ncoils, newton_steps=W.newton_steps, cg_iters=W.cg_iters, alpha0=W.alpha0,
                 alpha_q=W.alpha_q, sobolev_a=W.sobolev_a, sobolev_l=W.sobolev_l, use_graph=True, device=dev)
     ys, masks = build_series(torch, ctx, W, frames, dev)
-    tuned = ctx.autotune(ys[0], masks[0], reps=3)   # launch shapes from timed whole-frame graph replays
+    if args.no_autotune:
+        tuned = {"vec_blocks_per_sm": None, "pdl": None, "candidates": "not run (--no-autotune): compiled defaults"}
+    else:
+        tuned = ctx.autotune(ys[0], masks[0], reps=3)   # launch shapes from timed whole-frame graph replays
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = torch.empty(max(2 * l2, 256 << 20), dtype=torch.uint8, device=dev)
     x = torch.zeros((1 + W.ncoils, W.n, W.n), dtype=torch.complex64, device=dev)
