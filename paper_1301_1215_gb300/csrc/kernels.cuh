@@ -256,9 +256,9 @@ constexpr int kRowCtasPerSM = 2;
 // plane after its rows, all of its threads working on it.  A thread takes two pixels per step (o and
 // o + blockDim.x) and issues every load of both before the first use; the coil sum of a pixel runs over even and
 // odd coils in two partial sums added at the end.
-template <int N, int MODE>
+template <int N, int MODE, bool STDF>
 __device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
-  const int f = A.f, Wc = A.Wc, J = A.J;
+  const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc, J = A.J;
   constexpr long plane = (long)N * N;
   const long e_begin = (long)bid * A.rho_per_cta;
   const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
@@ -330,7 +330,7 @@ __device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
 // Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
@@ -342,7 +342,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   const int laneA = threadIdx.x / N1, idxA = threadIdx.x % N1;
   const bool mapA = (int)threadIdx.x < LANES * N1;
   const int laneB = threadIdx.x / N2, idxB = threadIdx.x % N2;
-  const int f = A.f, Wc = A.Wc;
+  const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc;
   float acc = 0.f;
   const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
   float2* smA = (float2*)(smem_raw + L.xch) + laneA * S::SM_LANE;
@@ -359,7 +359,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
   const bool activeA = mapA && RA < r_end, activeB = RB < r_end;
-  const int e1A = RA % N, e1B = RB % N;
+  const int e1A = RA % N;
   float2 v[E];
 
   // ---- direction update: the rows of r go to the exchange buffer (natural order, pitch N) while p is loaded
@@ -530,7 +530,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   __syncthreads();       // the next round restages the side rows
   }  // rounds
 
-  if constexpr (T::has_rho) acc += rho_slice<N, MODE>(A, bid);
+  if constexpr (T::has_rho) acc += rho_slice<N, MODE, STDF>(A, bid);
   if constexpr (T::reduces) {
     if (MODE == ROW_FFT_W_NORMAL && A.pq_part) {
       __shared__ double red[32];
@@ -542,11 +542,11 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   }
 }
 
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
-  row_pass_body<N1, N2, MODE>(A, blockIdx.x, gridDim.x, smem_raw);
+  row_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----
@@ -610,12 +610,12 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
   }
 }
 
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
-  const int f = A.f, Wc = A.Wc;
+  const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc;
   const int strips = (Wc + C - 1) / C;
   const int j = bid / strips;
   const int cc0 = (bid % strips) * C;
@@ -729,11 +729,11 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
   }
 }
 
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
-  col_pass_body<N1, N2, MODE>(A, blockIdx.x, smem_raw);
+  col_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, smem_raw);
 }
 
 // --------------------------------------------------------------------------------------------- batches ----
@@ -775,22 +775,22 @@ __device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int& bid
   return sa;
 }
 
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   int bid, nblk;
   const KArgs& A = batch_frame(B, bid, nblk);
-  row_pass_body<N1, N2, MODE>(A, bid, nblk, smem_raw);
+  row_pass_body<N1, N2, MODE, STDF>(A, bid, nblk, smem_raw);
 }
 
-template <int N1, int N2, int MODE>
+template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   int bid, nblk;
   const KArgs& A = batch_frame(B, bid, nblk);
-  col_pass_body<N1, N2, MODE>(A, bid, smem_raw);
+  col_pass_body<N1, N2, MODE, STDF>(A, bid, smem_raw);
 }
 
 // ------------------------------------------------------------------------------- per-size kernel table ----
@@ -804,6 +804,12 @@ struct SizeKernels {
   const void* col[NUM_COL_MODES];
   const void* row_batch[NUM_ROW_MODES];
   const void* col_batch[NUM_COL_MODES];
+  // Passes of the CG iteration specialised for the standard field of view f = N/4 (a compile-time constant, so
+  // the Omega tests of the register-held elements fold away); nullptr where the generic kernel is used.
+  const void* row_std[NUM_ROW_MODES];
+  const void* col_std[NUM_COL_MODES];
+  const void* row_std_batch[NUM_ROW_MODES];
+  const void* col_std_batch[NUM_COL_MODES];
   size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
   size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane_col, Wc).total; }
 };
@@ -862,6 +868,14 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.col_batch[COL_SIM_FFT] = (const void*)col_pass_batch<N1, N2, COL_SIM_FFT>;
   s.col_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT>;
   s.col_batch[COL_IFFT_ADJ_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_ADJ_FFT>;
+  // measured: the PSF and normal-operator row passes and the DF column pass gain from the constant field of
+  // view; the p-update row pass and the DF^H column pass do not
+  s.row_std[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF, true>;
+  s.row_std[ROW_FFT_W_NORMAL] = (const void*)row_pass<N1, N2, ROW_FFT_W_NORMAL, true>;
+  s.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, true>;
+  s.row_std_batch[ROW_PSF] = (const void*)row_pass_batch<N1, N2, ROW_PSF, true>;
+  s.row_std_batch[ROW_FFT_W_NORMAL] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_NORMAL, true>;
+  s.col_std_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT, true>;
   return s;
 }
 

@@ -225,6 +225,7 @@ struct nlinv_ctx {
   };
   std::vector<Rec>* rec = nullptr;   // non-null: launches are recorded instead of issued
   bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
+  bool std_fov = false;       // fov = N/4: the passes specialised for it (SizeKernels::row_std, col_std) apply
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   float2* ckpt = nullptr;     // non-null: q_reconstruct writes x_0 .. x_N here (nlinv_reconstruct_checkpoints)
   void* vjp_base = nullptr;   // scratch of nlinv_reconstruct_vjp (allocated on first use)
@@ -317,13 +318,15 @@ cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
   a.rows_per_cta = g.rows_per_cta;
   a.rho_per_cta = g.rho_per_cta;
   void* args[] = {&a};
-  return launch(c, c->k->row[mode], g.blocks, g.lanes * c->k->tl, c->k->row_smem(mode, g.lanes), args);
+  const void* fn = (c->std_fov && c->k->row_std[mode]) ? c->k->row_std[mode] : c->k->row[mode];
+  return launch(c, fn, g.blocks, g.lanes * c->k->tl, c->k->row_smem(mode, g.lanes), args);
 }
 
 cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J;
   void* args[] = {&a};
-  return launch(c, c->k->col[mode], col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
+  const void* fn = (c->std_fov && c->k->col_std[mode]) ? c->k->col_std[mode] : c->k->col[mode];
+  return launch(c, fn, col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
 }
 
 // c_j = W^-1 chat_j on Omega, for the coil planes of x (1+J planes).
@@ -638,6 +641,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->J = params->ncoils;
   c->f = params->fov;
   c->Wc = 2 * params->fov;
+  c->std_fov = 4 * params->fov == params->n;
   c->plane = (long)c->N * c->N;
   c->vec = (long)(1 + c->J) * c->plane;
   c->k = nlv::find_size(c->N);
@@ -680,10 +684,14 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) {
     allow(c->k->row[m], c->k->row_smem(m, lanes_max));
     if (smem_err.empty()) allow(c->k->row_batch[m], c->k->row_smem(m, lanes_max));
+    if (smem_err.empty() && c->k->row_std[m]) allow(c->k->row_std[m], c->k->row_smem(m, lanes_max));
+    if (smem_err.empty() && c->k->row_std_batch[m]) allow(c->k->row_std_batch[m], c->k->row_smem(m, lanes_max));
   }
   for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) {
     allow(c->k->col[m], c->k->col_smem(m, c->Wc));
     if (smem_err.empty()) allow(c->k->col_batch[m], c->k->col_smem(m, c->Wc));
+    if (smem_err.empty() && c->k->col_std[m]) allow(c->k->col_std[m], c->k->col_smem(m, c->Wc));
+    if (smem_err.empty() && c->k->col_std_batch[m]) allow(c->k->col_std_batch[m], c->k->col_smem(m, c->Wc));
   }
   if (!smem_err.empty()) {
     cudaGetLastError();
@@ -1305,10 +1313,14 @@ void batch_free(nlinv_batch* b) {
 
 // The batched kernel that runs the single-frame pass fn for several frames.
 const void* batched_kernel(const SizeKernels* k, const void* fn) {
-  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m)
+  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m) {
     if (fn == k->row[m]) return k->row_batch[m];
-  for (int m = 0; m < nlv::NUM_COL_MODES; ++m)
+    if (k->row_std[m] && fn == k->row_std[m]) return k->row_std_batch[m];
+  }
+  for (int m = 0; m < nlv::NUM_COL_MODES; ++m) {
     if (fn == k->col[m]) return k->col_batch[m];
+    if (k->col_std[m] && fn == k->col_std[m]) return k->col_std_batch[m];
+  }
   if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
   if (fn == (const void*)add_kernel) return (const void*)add_batch;
   return nullptr;
