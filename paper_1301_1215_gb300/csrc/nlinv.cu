@@ -9,6 +9,10 @@
 //                         col COL_IFFT_ADJ_FFT, row ROW_FFT_W_NORMAL (+ Re<p, q>)
 //   CG updates     dx += alpha p, r -= alpha q (+ |r|^2); p = r + beta p
 // Each operator application performs the two 2D transforms per operator of Table 1, batched over all coils.
+// Beyond the paper's method: the gradient through the reconstruction (nlinv_reconstruct_checkpoints and
+// nlinv_reconstruct_vjp: the same operators at other linearisation points, plus a CG solve per Newton step),
+// batches of independent frames (nlinv_batch_*: the same passes, one launch per grid side), and the launch-shape
+// autotuner (nlinv_autotune: whole graph-replayed frames per candidate).
 #include <algorithm>
 #include <chrono>
 #include <cmath>

@@ -246,8 +246,8 @@ class Nlinv:
                   "cg step")
 
     def profile_cg(self, reps: int = 20) -> dict:
-        """Mean CUDA-event duration (ms) of each kernel of one CG iteration, launched one by one on the state of
-        the last reconstruction (advances its CG state)."""
+        """Steady-state CUDA-event duration (ms) of each kernel of one CG iteration: each is launched ``reps``
+        times back to back on the state of the last reconstruction (which it advances), as in a graph replay."""
         ms = (C.c_double * len(self.CG_KERNELS))()
         self._begin()
         self._check(self._lib.nlinv_profile_cg(self._h, int(reps), ms))
