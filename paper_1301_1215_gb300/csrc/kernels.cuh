@@ -94,11 +94,6 @@ __device__ __forceinline__ bool in_omega(int e, int N, int f) { return e < f || 
 __device__ __forceinline__ int to_compact(int e, int N, int f) { return e < f ? e : e - (N - 2 * f); }
 __device__ __forceinline__ int to_natural(int cc, int N, int f) { return cc < f ? cc : cc + (N - 2 * f); }
 
-// Sobolev weight of W (Sec. 3.1) at natural index (k1, k2), from the table built on the host in double precision.
-__device__ __forceinline__ float sobolev_w(int k1, int k2, const KArgs& A) {
-  return __ldg(&A.wtab[(size_t)k1 * A.N + k2]);
-}
-
 // beta of the pending direction update p = r + beta p (CG, Table 1)
 __device__ __forceinline__ float cg_beta(const KArgs& A) { return (float)A.sc->beta; }
 
