@@ -78,6 +78,35 @@ def test_null_context_is_rejected(lib):
     assert lib.nlinv_last_launch_count(None) == -1
 
 
+def test_every_context_call_rejects_a_null_context(lib):
+    """Each entry point that takes a context (or batch) answers a NULL one on the host, before any CUDA call."""
+    from paper_1301_1215_gb300 import _lib
+    E = _lib.EINVAL
+    assert lib.nlinv_derivative(None, None, None, None, None) == E
+    assert lib.nlinv_adjoint(None, None, None, None, None) == E
+    assert lib.nlinv_normal(None, None, None, None, 1.0, None) == E
+    assert lib.nlinv_image(None, None, None) == E
+    assert lib.nlinv_simulate(None, None, None, None, None) == E
+    assert lib.nlinv_reconstruct_checkpoints(None, None, None, None, None, None, None) == E
+    assert lib.nlinv_reconstruct_vjp(None, None, None, None, None, 0, None, None, None) == E
+    ms = (C.c_double * 6)()
+    assert lib.nlinv_profile_cg(None, 1, ms) == E
+    assert lib.nlinv_autotune(None, None, None, None, 3, None, None, 0) == E
+    assert lib.nlinv_reconstruct_batch(None, 0, None) == E
+    assert lib.nlinv_batch_launch_count(None) == -1
+    assert lib.nlinv_batch_destroy(None) == _lib.OK
+
+
+def test_batch_create_rejects_bad_arguments_on_the_host(lib):
+    from paper_1301_1215_gb300 import _lib
+    p = _lib.Params()
+    lib.nlinv_default_params(C.byref(p), 64, 4)
+    h = C.c_void_p()
+    assert lib.nlinv_batch_create(C.byref(p), 0, None, None, C.byref(h)) == _lib.EINVAL
+    assert lib.nlinv_batch_create(None, 1, None, None, C.byref(h)) == _lib.EINVAL
+    assert lib.nlinv_batch_create(C.byref(p), 1, None, None, None) == _lib.EINVAL
+
+
 def test_create_without_gpu_reports_cuda_error(lib):
     import torch
     if torch.cuda.is_available():
