@@ -86,7 +86,8 @@ NLINV_API nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils);
  * 9 (1+J) n^2 complex values) and builds the transform tables.  stream is a cudaStream_t on which the context
  * queues its work; NULL makes the context create (and later destroy) a non-blocking stream of its own, since the
  * legacy default stream cannot be captured into a graph.  On success *out owns the context.  Blocks until set-up
- * is done.  Errors: EINVAL (bad params, NULL out), ENOMEM, ECUDA. */
+ * is done.  Errors: EINVAL (bad params, NULL out), ENOMEM (the workspace allocation failed; the environment
+ * variable NLINV_TEST_FAIL_ALLOC=1, for tests, makes it fail without trying), ECUDA. */
 NLINV_API nlinv_status nlinv_create(const nlinv_params* params, void* stream, nlinv_ctx** out);
 
 /* Waits for the context's stream, then frees the context and its workspace.  NULL is accepted. */

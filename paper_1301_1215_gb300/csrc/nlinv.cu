@@ -718,9 +718,13 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
   const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 3 * partb + scb;
-  e = cudaMalloc(&c->base, total);
+  // NLINV_TEST_FAIL_ALLOC=1 (tests only): the workspace allocation reports out-of-memory without trying, so that
+  // the ENOMEM path can be exercised without exhausting a GPU.
+  const char* fail_alloc = std::getenv("NLINV_TEST_FAIL_ALLOC");
+  e = (fail_alloc && std::strcmp(fail_alloc, "1") == 0) ? cudaErrorMemoryAllocation : cudaMalloc(&c->base, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    c->base = nullptr;
     g_create_error = "cudaMalloc of " + std::to_string(total) + " bytes failed: " + cudaGetErrorString(e);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;

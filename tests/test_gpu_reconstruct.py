@@ -157,6 +157,22 @@ def test_nan_data_reports_breakdown(torch_cuda):
         ctx.wait(-1)       # the flag was cleared by the failing call
 
 
+def test_workspace_allocation_failure_reports_enomem(torch_cuda, monkeypatch):
+    """A failed workspace allocation (injected on the host) is ENOMEM with a message, and leaves the device usable."""
+    torch = torch_cuda
+    from paper_1301_1215_gb300 import _lib
+    from paper_1301_1215_gb300.nlinv import Nlinv, NlinvError
+    monkeypatch.setenv("NLINV_TEST_FAIL_ALLOC", "1")
+    with pytest.raises(NlinvError) as ei:
+        Nlinv(64, 4)
+    assert ei.value.status == _lib.ENOMEM and "cudaMalloc" in str(ei.value)
+    monkeypatch.delenv("NLINV_TEST_FAIL_ALLOC")
+    with Nlinv(64, 4, newton_steps=1, cg_iters=1) as ctx:
+        n, J = 64, 4
+        s, fr, y = noisy_data(n, J, 16, 11)
+        assert np.isfinite(ctx.reconstruct(_t(torch, y), _t(torch, fr.mask)).cpu().numpy()).all()
+
+
 def test_wait_deadline(torch_cuda):
     torch = torch_cuda
     from paper_1301_1215_gb300 import _lib
