@@ -138,6 +138,31 @@ def simulate(s: Setup, mask: np.ndarray, rho: np.ndarray, coil_img: np.ndarray) 
     return mask * fft2u(M * rho * coil_img)
 
 
+def grid_radial(n: int, angles, samples: np.ndarray):
+    """Interpolation of radial samples onto the n x n grid: the CPU pre-processing step of Sec. 3.1 that the paper
+    leaves unspecified, read as nearest-neighbour gridding with averaging.  Sample i of spoke s lies at
+    t_i (cos theta_s, sin theta_s), t_i = -n/2 + i/2 (i < 2n); each coordinate goes to the grid point floor(v + 1/2)
+    and the sample is kept when both lie in [-n/2, n/2).  A grid point (row = ky, column = kx, natural order) holds
+    the mean of its samples; the sampling pattern marks the points that received at least one.
+    samples: (J, S, 2n).  Returns (y (J, n, n), mask (n, n) uint8)."""
+    samples = np.asarray(samples, dtype=np.complex128)
+    J = samples.shape[0]
+    total = np.zeros((J, n, n), dtype=np.complex128)
+    count = np.zeros((n, n), dtype=np.int64)
+    for si, th in enumerate(angles):
+        for i in range(2 * n):
+            t = -n / 2 + 0.5 * i
+            kx = int(np.floor(t * np.cos(th) + 0.5))
+            ky = int(np.floor(t * np.sin(th) + 0.5))
+            if -n // 2 <= kx < n // 2 and -n // 2 <= ky < n // 2:
+                total[:, ky % n, kx % n] += samples[:, si, i]
+                count[ky % n, kx % n] += 1
+    hit = count > 0
+    y = np.zeros_like(total)
+    y[:, hit] = total[:, hit] / count[hit]
+    return y, hit.astype(np.uint8)
+
+
 def image(s: Setup, x: np.ndarray) -> np.ndarray:
     """Coil-combined image rho * sqrt(sum_j |c_j|^2) on Omega, centred (row i holds the signed coordinate i - fov):
     the customary NLINV output, which removes the rho -> s rho, c -> c / s ambiguity up to a phase.  The paper does

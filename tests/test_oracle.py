@@ -435,3 +435,37 @@ def test_irgnm_vjp_ignores_data_outside_the_mask():
     xs, alphas = O.irgnm_path(s, mask, y, x0, xref, 2, 250)
     gy = O.irgnm_vjp(s, mask, y, xs, alphas, g, 250)[0]
     assert not gy[:, mask == 0].any()
+
+
+# ----------------------------------------------------------------------------------------------- gridding ----
+
+@pytest.mark.parametrize("n,spokes,rot", [(16, 5, 0.0), (64, 16, 0.3), (96, 13, 1.1)])
+def test_gridding_pattern_is_the_rasterised_mask(n, spokes, rot):
+    """Two independent statements of the spoke rasterisation agree: the gridder's pattern and the input
+    generator's sampling mask."""
+    angles = [np.pi * k / spokes + rot for k in range(spokes)]
+    rng = synth.rng_for(61)
+    _, mask = O.grid_radial(n, angles, synth.random_complex((2, spokes, 2 * n), rng))
+    assert np.array_equal(mask, synth.radial_mask(n, spokes, rot))
+
+
+def test_gridding_of_one_horizontal_spoke_by_hand():
+    """n = 8, one spoke at angle 0: t = -4, -3.5, ..., 3.5 round to kx = -4, -3, -3, -2, -2, ..., 3, 3 and 4 (dropped),
+    so column k (-3..3) of row 0 holds the mean of samples 2k+7 and 2k+8, column -4 sample 0 alone."""
+    rng = synth.rng_for(62)
+    smp = synth.random_complex((2, 1, 16), rng)
+    y, mask = O.grid_radial(8, [0.0], smp)
+    want = np.zeros((2, 8, 8), complex)
+    want[:, 0, (-4) % 8] = smp[:, 0, 0]
+    for k in range(-3, 4):
+        want[:, 0, k % 8] = 0.5 * (smp[:, 0, 2 * k + 7] + smp[:, 0, 2 * k + 8])
+    assert np.allclose(y, want, rtol=0, atol=1e-15)
+    assert mask.sum() == 8 and mask[0].all()
+
+
+def test_gridding_of_identical_samples_is_that_value():
+    angles = [np.pi * k / 7 for k in range(7)]
+    smp = np.full((3, 7, 64), 0.25 - 0.5j)
+    y, mask = O.grid_radial(32, angles, smp)
+    assert np.allclose(y[:, mask == 1], 0.25 - 0.5j, rtol=0, atol=1e-15)
+    assert not y[:, mask == 0].any()
