@@ -278,6 +278,26 @@ def run_ours(args, rank, world, local):
         e2e = {"value": round(world * K / tot, 3), "unit": "frames/s", "h2d_bytes_per_step": int(bi),
                "d2h_bytes_per_step": int(xh.numel() * 8)}
 
+    # the gridding of one frame's radial samples onto the grid (nlinv_grid, the pre-processing of Sec. 3.1)
+    from paper_1301_1215_gb300.nlinv import Gridder
+    ang = [np.pi * s_ / W.spokes + synth.frame_rotation(0, W.spokes) for s_ in range(W.spokes)]
+    with Gridder(W.n, [(np.cos(a), np.sin(a)) for a in ang], device=dev) as gr:
+        smp = torch.randn((W.ncoils, W.spokes, 2 * W.n), dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            gr.grid(smp)
+        torch.cuda.synchronize()
+        gs, ge = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gs.record(gr.stream)
+        for _ in range(100):
+            gr.grid(smp)
+        ge.record(gr.stream)
+        torch.cuda.synchronize()
+        grid_us = gs.elapsed_time(ge) / 100 * 1e3
+    gbytes = smp.numel() * 8 + W.ncoils * W.n * W.n * 8 + W.n * W.n
+    gridding = {"workload": f"{W.spokes} spokes x {2 * W.n} samples x {W.ncoils} coils onto {W.n}^2",
+                "us_per_frame": round(grid_us, 2), "algo_bytes": int(gbytes),
+                "gbs": round(gbytes / (grid_us * 1e-6) / 1e9, 1)}
+
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak",
@@ -295,7 +315,7 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": src, "traffic": traffic,
                      "algo_bytes_per_launch": int(algo[top]), "kernels": kernels},
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "finite": finite,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "finite": finite, "gridding": gridding,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(W)

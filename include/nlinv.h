@@ -165,6 +165,31 @@ NLINV_API nlinv_status nlinv_reconstruct_vjp(nlinv_ctx* ctx, const nlinv_c32* y,
                                              const nlinv_c32* ckpt, const nlinv_c32* grad_x, int tied,
                                              nlinv_c32* grad_y, nlinv_c32* grad_x0, nlinv_c32* grad_xref);
 
+/* --------------------------------------------------------------------------------------------- gridding ----
+ * Sec. 3.1 interpolates the measured radial samples onto the Cartesian grid on the CPU before the reconstruction,
+ * without saying how.  Here it runs on the GPU as nearest-neighbour gridding with averaging: sample i of spoke s
+ * lies at t_i d_s with t_i = -n/2 + i/2 (i < 2n) and d_s the spoke's unit direction; each coordinate goes to the
+ * grid point floor(v + 1/2), the sample is kept when both lie in [-n/2, n/2), and a grid point (row = ky,
+ * column = kx, natural FFT order) holds the mean of its samples (0 if none); the sampling pattern marks the grid
+ * points that received a sample.  With the spoke angles of the real-time series this pattern is the one the
+ * reconstruction's mask describes. */
+typedef struct nlinv_gridder nlinv_gridder;
+
+/* Builds the gridding of nspokes spokes of 2n samples on the n x n grid (n even, 8..2048).  directions (HOST,
+ * 2 * nspokes doubles): (cos, sin) of each spoke's angle.  stream: a cudaStream_t, or NULL for a stream of its own.
+ * Errors: EINVAL, ENOMEM, ECUDA (message in nlinv_last_error(NULL)). */
+NLINV_API nlinv_status nlinv_gridder_create(int n, int nspokes, const double* directions, void* stream,
+                                            nlinv_gridder** out);
+
+/* y_out (DEVICE, ncoils x n x n) and mask_out (DEVICE, n x n) from samples (DEVICE, ncoils x nspokes x 2n, spoke-major
+ * within a coil).  Queued on the gridder's stream.  Errors: EINVAL (NULL or host pointers, ncoils outside 1..64),
+ * ECUDA. */
+NLINV_API nlinv_status nlinv_grid(nlinv_gridder* g, int ncoils, const nlinv_c32* samples, nlinv_c32* y_out,
+                                  uint8_t* mask_out);
+
+/* Waits for the gridder's stream and frees it.  NULL is accepted. */
+NLINV_API nlinv_status nlinv_gridder_destroy(nlinv_gridder* g);
+
 /* ---------------------------------------------------------------------------------------------- batches ----
  * Many independent frames (slices, series of different patients, ...) of uneven grid side and coil count,
  * reconstructed together: every pass of Eq. 3 is one launch per grid side covering all frames of that side, and

@@ -57,6 +57,9 @@ SIGNATURES = {
     "nlinv_batch_launch_count": (_long, [_vp]),
     "nlinv_batch_destroy": (_int, [_vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
+    "nlinv_gridder_create": (_int, [_int, _int, C.POINTER(_dbl), _vp, C.POINTER(_vp)]),
+    "nlinv_grid": (_int, [_vp, _int, _vp, _vp, _vp]),
+    "nlinv_gridder_destroy": (_int, [_vp]),
     "nlinv_autotune": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(Tuning), C.POINTER(Tuning), _int]),
     "nlinv_last_error": (C.c_char_p, [_vp]),
 }

@@ -371,3 +371,58 @@ class NlinvBatch:
         if resid:
             return xs, [[float(v) for v in b] for b in bufs]
         return xs
+
+
+class Gridder:
+    """Nearest-neighbour gridding of radial spokes onto the n x n grid with averaging (nlinv_gridder_create /
+    nlinv_grid): the interpolation that Sec. 3.1 performs before the reconstruction.  ``directions``: (S, 2) array of
+    (cos, sin) of the spoke angles.  :meth:`grid` maps samples (J, S, 2n) complex64 on the device to the gridded data
+    (J, n, n) and the sampling pattern (n, n) uint8."""
+
+    def __init__(self, n: int, directions, device=None):
+        import numpy as np
+        self._lib = _lib.load()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        if dev.type != "cuda" or not torch.cuda.is_available():
+            raise RuntimeError("the NLINV library needs a CUDA device")
+        self.device = dev if dev.index is not None else torch.device("cuda", torch.cuda.current_device())
+        d = np.ascontiguousarray(np.asarray(directions, dtype=np.float64).reshape(-1, 2))
+        self.n, self.nspokes = int(n), int(d.shape[0])
+        self.stream = torch.cuda.Stream(device=self.device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._lib.nlinv_gridder_create(self.n, self.nspokes,
+                                                      d.ctypes.data_as(C.POINTER(C.c_double)),
+                                                      C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self._h = h
+
+    def grid(self, samples: torch.Tensor):
+        if not isinstance(samples, torch.Tensor) or samples.device != self.device or samples.dtype != torch.complex64:
+            raise TypeError(f"samples must be a complex64 tensor on {self.device}")
+        if samples.dim() != 3 or tuple(samples.shape[1:]) != (self.nspokes, 2 * self.n):
+            raise ValueError(f"samples must have shape (J, {self.nspokes}, {2 * self.n})")
+        samples = samples.contiguous()
+        J = samples.shape[0]
+        y = torch.empty((J, self.n, self.n), dtype=torch.complex64, device=self.device)
+        m = torch.empty((self.n, self.n), dtype=torch.uint8, device=self.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+        _lib.check(self._lib.nlinv_grid(self._h, int(J), _ptr(samples), _ptr(y), _ptr(m)))
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        return y, m
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.nlinv_gridder_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

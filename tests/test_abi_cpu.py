@@ -97,6 +97,20 @@ def test_every_context_call_rejects_a_null_context(lib):
     assert lib.nlinv_batch_destroy(None) == _lib.OK
 
 
+def test_gridder_create_rejects_bad_arguments_on_the_host(lib):
+    from paper_1301_1215_gb300 import _lib
+    d = (C.c_double * 2)(1.0, 0.0)
+    h = C.c_void_p()
+    assert lib.nlinv_gridder_create(7, 1, d, None, C.byref(h)) == _lib.EINVAL       # odd n
+    assert lib.nlinv_gridder_create(4, 1, d, None, C.byref(h)) == _lib.EINVAL       # too small
+    assert lib.nlinv_gridder_create(16, 0, d, None, C.byref(h)) == _lib.EINVAL      # no spokes
+    assert lib.nlinv_gridder_create(16, 1, None, None, C.byref(h)) == _lib.EINVAL   # no directions
+    nan = (C.c_double * 2)(float("nan"), 0.0)
+    assert lib.nlinv_gridder_create(16, 1, nan, None, C.byref(h)) == _lib.EINVAL
+    assert lib.nlinv_grid(None, 1, None, None, None) == _lib.EINVAL
+    assert lib.nlinv_gridder_destroy(None) == _lib.OK
+
+
 def test_batch_create_rejects_bad_arguments_on_the_host(lib):
     from paper_1301_1215_gb300 import _lib
     p = _lib.Params()
