@@ -345,10 +345,16 @@ def cpu_baseline(W):
     O.irgnm(s, fr.mask, y, x0, None, 1, W.cg_iters)
     dt = time.perf_counter() - t0
     cores = max(1, round((cpu_seconds() - c0) / dt))
+    # one application of the normal operator (DF^H DF + alpha) on the same problem, coil maps given
+    c = O.coils(s, x0)
+    t1 = time.perf_counter()
+    O.normal(s, fr.mask, x0, x0, W.alpha0, c)
+    normal_ms = (time.perf_counter() - t1) * 1e3
     return {"value": round(1.0 / (dt * W.newton_steps), 6), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "host_cores": os.cpu_count(),
+            "host_cores": os.cpu_count(), "normal_op_ms": round(normal_ms, 1),
             "sample": f"Newton step 0 of frame 0 ({W.cg_iters} CG iterations, numpy complex128), "
-                      f"{dt:.2f} s, scaled x{W.newton_steps} to one frame"}
+                      f"{dt:.2f} s, scaled x{W.newton_steps} to one frame; normal_op_ms: one (DF^H DF + alpha) "
+                      f"application on the same frame"}
 
 
 def cpu_seconds() -> float:
