@@ -27,6 +27,13 @@
  *   - Unless stated otherwise, pointers are DEVICE pointers owned by the caller, valid until the work is done.
  *   - No entry point throws; every one returns an nlinv_status.  Arguments are checked on the host before any
  *     work is queued; on error nothing is queued and nlinv_last_error() describes the problem.
+ *
+ * Entry points, in the order below: contexts (nlinv_default_params, nlinv_create, nlinv_destroy); the operators
+ * F, DF, DF^H, DF^H DF + alpha, the display image and data synthesis; the reconstruction of Eq. 3
+ * (nlinv_reconstruct) and the gradient through it (nlinv_reconstruct_checkpoints, nlinv_reconstruct_vjp);
+ * gridding of radial samples (nlinv_gridder_*); batches of independent frames (nlinv_batch_*); waiting,
+ * per-kernel timing, the launch-shape autotuner and launch counts; F without a context or allocation
+ * (nlinv_forward_noalloc); error messages.
  */
 #ifndef NLINV_H
 #define NLINV_H
