@@ -13,8 +13,10 @@ library primitive.  Where the paper leaves a detail open, the reading taken here
 * the Sobolev weight of ``W`` is ``w(k) = (1 + a |k|^2)^(-l/2)`` with ``|k|`` in cycles per grid width,
   ``k_i = g(i)/n`` in ``[-1/2, 1/2)``;
 * Omega is the centred square ``-fov <= g < fov`` (the un-oversampled image of a 2x grid, Sec. 3.2);
-* CG runs a fixed number of iterations from ``dx = 0`` and stops early only at the rounding floor
-  (``|r|^2 = 0`` or ``Re<p, A p> <= 0``, impossible in exact arithmetic for the positive definite system);
+* CG runs a fixed number of iterations from ``dx = 0`` and stops early only at the rounding floor of the
+  single-precision arithmetic the method runs in (Sec. 3.2): ``|r| <= 2^-24 |b|`` (the unit roundoff of FP32),
+  ``Re<p, A p> <= 0`` or a non-finite value -- none of which occurs in exact arithmetic for the positive definite
+  system before the solution is reached; once stopped, the rest of that solve leaves dx unchanged;
 * ``alpha_n = max(alpha_0 q^n, alpha_min)``; a single frame regularises toward its start value.
 """
 from __future__ import annotations
@@ -177,23 +179,37 @@ def image(s: Setup, x: np.ndarray) -> np.ndarray:
 # Conjugate gradients and the iteratively regularised Gauss-Newton method (Eq. 3)
 # ---------------------------------------------------------------------------------------------------------------
 
-def cg(apply_A, b: np.ndarray, iters: int) -> np.ndarray:
+# Rounding floor of CG: |r|^2 <= CG_FLOOR2 |b|^2 with 2^-24 the unit roundoff of the FP32 arithmetic (Sec. 3.2).
+CG_FLOOR2 = 2.0 ** -48
+
+
+def cg(apply_A, b: np.ndarray, iters: int, info: dict | None = None, floor2: float = CG_FLOOR2) -> np.ndarray:
     """Conjugate gradients for A dx = b, A Hermitian positive definite, from dx = 0, for a fixed count.
 
     Per iteration (Table 1, row CG: two scalar products): q = A p; alpha = |r|^2 / Re<p, q>; dx += alpha p;
-    r -= alpha q; beta = |r_new|^2 / |r|^2; p = r + beta p.  Stops early only when |r|^2 = 0 or Re<p, q> <= 0:
-    for the positive definite system of Eq. 3 both mean that the iteration has reached the rounding floor.
+    r -= alpha q; beta = |r_new|^2 / |r|^2; p = r + beta p.  Stops early only at the rounding floor of the
+    single-precision method: |r|^2 <= floor2 |b|^2 (floor2 = CG_FLOOR2 = 2^-48, |r| at the FP32 unit roundoff
+    relative to |b|; this includes b = 0), Re<p, q> <= 0, or a non-finite value.  No later iteration of this solve
+    changes dx.  ``info``, if given, receives ``info["stop"]``: the index of the iteration that stopped, or -1 when
+    all ``iters`` iterations ran.  ``floor2 = 0`` gives plain CG (stopping only at |r| = 0).
     """
     dx = np.zeros_like(b)
     r = b.copy()
     p = r.copy()
     rr = inner(r, r).real
-    for _ in range(iters):
-        if rr == 0.0:
+    rr0 = rr
+    if info is not None:
+        info["stop"] = -1
+    for it in range(iters):
+        if not (rr > floor2 * rr0 and np.isfinite(rr)):
+            if info is not None:
+                info["stop"] = it
             break
         q = apply_A(p)
         pq = inner(p, q).real
-        if not pq > 0.0:
+        if not (pq > 0.0 and np.isfinite(pq)):
+            if info is not None:
+                info["stop"] = it
             break
         a = rr / pq
         dx = dx + a * p
@@ -217,31 +233,36 @@ def alpha_schedule(newton_steps: int, alpha0: float, q: float, alpha_min: float 
 
 
 def irgnm(s: Setup, mask: np.ndarray, y: np.ndarray, x0: np.ndarray, xref: np.ndarray | None,
-          newton_steps: int, cg_iters: int, alpha0: float = 1.0, q: float = 0.5, alpha_min: float = 0.0):
+          newton_steps: int, cg_iters: int, alpha0: float = 1.0, q: float = 0.5, alpha_min: float = 0.0,
+          cg_stops: list | None = None):
     """Iteratively regularised Gauss-Newton method (Eq. 3).
 
     For n = 0 .. newton_steps-1: b = DF^H(y - F x_n) - alpha_n (x_n - x_ref); solve
     (DF^H DF + alpha_n I) dx = b by ``cg_iters`` CG iterations; x_{n+1} = x_n + dx.
     ``xref=None`` regularises toward x0.  Returns x_N and the residual norms |y - F x_n| for n = 0 .. N.
+    ``cg_stops``, if given, receives per Newton step the CG iteration that reached the rounding floor (-1: none).
     """
     x = np.array(x0, dtype=np.complex128, copy=True)
     xr = x.copy() if xref is None else np.asarray(xref, dtype=np.complex128)
     norms = []
     for alpha in alpha_schedule(newton_steps, alpha0, q, alpha_min):
-        x, nr = newton_step(s, mask, y, x, xr, alpha, cg_iters)
+        info = {}
+        x, nr = newton_step(s, mask, y, x, xr, alpha, cg_iters, info)
         norms.append(nr)
+        if cg_stops is not None:
+            cg_stops.append(info["stop"])
     norms.append(residual(s, mask, y, x)[1])
     return x, norms
 
 
 def newton_step(s: Setup, mask: np.ndarray, y: np.ndarray, x: np.ndarray, xr: np.ndarray, alpha: float,
-                cg_iters: int):
+                cg_iters: int, info: dict | None = None):
     """One step of Eq. 3: b = DF^H(y - F x) - alpha (x - x_ref), (DF^H DF + alpha I) dx = b by CG, x + dx.
-    Returns the new iterate and |y - F x| at the old one."""
+    Returns the new iterate and |y - F x| at the old one (``info`` as for :func:`cg`)."""
     r0, nr = residual(s, mask, y, x)
     c = coils(s, x)
     b = adjoint(s, mask, x, r0, c) - alpha * (x - xr)
-    dx = cg(lambda d: normal(s, mask, x, d, alpha, c), b, cg_iters)
+    dx = cg(lambda d: normal(s, mask, x, d, alpha, c), b, cg_iters, info)
     return x + dx, nr
 
 

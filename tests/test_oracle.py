@@ -240,7 +240,7 @@ def test_cg_solves_small_hermitian_system():
     B = synth.random_complex((30, 20), rng)
     A = B.conj().T @ B + np.eye(20)
     b = synth.random_complex(20, rng)
-    dx = O.cg(lambda v: A @ v, b, 60)
+    dx = O.cg(lambda v: A @ v, b, 60, floor2=0.0)
     assert rel(dx, np.linalg.solve(A, b)) < 1e-10
 
 
@@ -251,8 +251,12 @@ def test_cg_on_dense_nlinv_system_matches_solve():
     mask = synth.radial_mask(8, 3)
     A = dense_normal(s, mask, x, 1.0)
     b = synth.random_complex((3, 8, 8), rng)
-    dx = O.cg(lambda v: O.normal(s, mask, x, v, 1.0), b, 400)
+    dx = O.cg(lambda v: O.normal(s, mask, x, v, 1.0), b, 400, floor2=0.0)
     assert rel(dx.ravel(), np.linalg.solve(A, b.ravel())) < 1e-9
+    # with the FP32 rounding floor the solve stops once |r| <= 2^-24 |b|: the solution to about that level
+    info = {}
+    dxf = O.cg(lambda v: O.normal(s, mask, x, v, 1.0), b, 400, info)
+    assert 0 < info["stop"] < 400 and rel(dxf.ravel(), np.linalg.solve(A, b.ravel())) < 1e-6
 
 
 def test_cg_zero_rhs_stays_zero():
