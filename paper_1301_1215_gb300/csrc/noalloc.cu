@@ -4,7 +4,7 @@
 // real-time loop that reserves all of its GPU memory up front and must not risk a cudaMalloc failing or stalling
 // mid-series, or a host framework that owns every device allocation and hands this library only its buffers.
 // Such callers cannot create an nlinv_ctx (nlinv_create allocates the workspace), so this entry point keeps its
-// scratch -- the Omega-column transform buffer, the coil maps, the twiddle and Sobolev tables -- in one
+// scratch -- the twiddle and Sobolev tables, the Omega-column transform buffer and the coil maps -- in one
 // file-scope __device__ array of fixed size (kScratchBytes).  Every GPU that loads the library holds that array
 // until the process exits.
 #include <cmath>
@@ -22,6 +22,16 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(16) << 20;   // 16 MiB: covers 384 x 384 with 10 coils at fov = n/4
 constexpr int kMaxDevices = 64;
+constexpr int kMaxSide = 512;                          // largest grid side with a compiled transform
+
+// Layout of the array: the tables first, at offsets fixed for every call (so that tables written by an earlier
+// call with the same n and Sobolev parameters are found where this call looks for them, whatever its coil count
+// and field of view), then the transform buffer T and the coil maps, whose sizes vary from call to call.
+constexpr size_t kTwOff = 0;                                             // twiddles of the split (N1, N2)
+constexpr size_t kTwBOff = kTwOff + size_t(kMaxSide) * 8;                // twiddles of the split (N2, N1)
+constexpr size_t kWOff = kTwBOff + size_t(kMaxSide) * 8;                 // Sobolev weight, n x n floats
+constexpr size_t kDataOff = kWOff + size_t(kMaxSide) * kMaxSide * 4;     // T, then the coil maps
+static_assert(kDataOff % 256 == 0, "the data region must stay 256-byte aligned");
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -42,13 +52,16 @@ nlinv_status fail(nlinv_status s, const std::string& msg) {
   return s;
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (the current device, which runs the kernels and holds the scratch array), or
+// managed memory.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at{};
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 cudaError_t launch(const void* fn, int grid, int block, size_t smem, cudaStream_t st, nlv::KArgs a) {
@@ -68,16 +81,13 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   if (!(p->sobolev_a >= 0) || !(p->sobolev_l >= 0) || !std::isfinite(p->sobolev_a) || !std::isfinite(p->sobolev_l))
     return fail(NLINV_EINVAL, "sobolev_a and sobolev_l must be finite and >= 0");
   if (!x || !mask || !y_out) return fail(NLINV_EINVAL, "x, mask and y_out must not be NULL");
-  if (!on_device(x) || !on_device(mask) || !on_device(y_out))
-    return fail(NLINV_EINVAL, "x, mask and y_out must be device pointers");
+  if (p->n > kMaxSide) return fail(NLINV_EINVAL, "grid side beyond the table region of the scratch array");
 
   const int N = p->n, J = p->ncoils, f = p->fov, Wc = 2 * f;
   const size_t plane = (size_t)N * N;
   const size_t bT = round256((size_t)J * N * Wc * sizeof(float2));
   const size_t bC = round256((size_t)J * Wc * Wc * sizeof(float2));
-  const size_t bTw = round256((size_t)N * sizeof(float2));
-  const size_t bW = round256(plane * sizeof(float));
-  const size_t need = bT + bC + 2 * bTw + bW;
+  const size_t need = kDataOff + bT + bC;
   if (need > kScratchBytes)
     return fail(NLINV_EINVAL, "nlinv_forward_noalloc needs " + std::to_string(need) +
                                   " bytes of scratch for this n, ncoils and fov; its static maximum is " +
@@ -87,6 +97,8 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(NLINV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(NLINV_EINVAL, "device ordinal out of range");
+  if (!on_device(x, dev) || !on_device(mask, dev) || !on_device(y_out, dev))
+    return fail(NLINV_EINVAL, "x, mask and y_out must be device (or managed) memory of the current device");
   cudaStream_t st = (cudaStream_t)stream;
 
   std::lock_guard<std::mutex> lock(g_mutex);
@@ -100,11 +112,11 @@ extern "C" NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* p, v
     ds.ready = true;
   }
   unsigned char* b = ds.base;
-  float2* T = (float2*)b;
-  float2* coil = (float2*)(b + bT);
-  float2* twA = (float2*)(b + bT + bC);
-  float2* twB = (float2*)(b + bT + bC + bTw);
-  float* wtab = (float*)(b + bT + bC + 2 * bTw);
+  float2* twA = (float2*)(b + kTwOff);
+  float2* twB = (float2*)(b + kTwBOff);
+  float* wtab = (float*)(b + kWOff);
+  float2* T = (float2*)(b + kDataOff);
+  float2* coil = (float2*)(b + kDataOff + bT);
 
   if (ds.n != N || ds.a != p->sobolev_a || ds.l != p->sobolev_l) {
     // tables for this grid side and weight: computed here, copied into the scratch array, then the stream is

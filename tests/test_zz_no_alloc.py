@@ -2,10 +2,11 @@
 
 Callers that may not allocate device memory when they apply F -- a real-time loop that reserved its GPU memory up
 front, or a host framework that owns every device allocation -- cannot create a context, so this entry point keeps
-its scratch in a fixed file-scope device array.  Checked through the C interface on two calls in a row (the second
-one with another grid side, so the tables in the shared array are rewritten), against the existing entry point
-within the operator tolerance of the other GPU tests, plus the size limit of the array.  This file is collected
-last so that a failure here does not hide any other test."""
+its scratch in a fixed file-scope device array.  Checked through the C interface on calls in a row against the
+existing entry point, within the operator tolerance of the other GPU tests: calls with the same grid side but
+other coil counts and fields of view (the tables written by the first call are reused, the buffers behind them
+change size), then another grid side (the tables are rewritten); plus the size limit of the array.  This file is
+collected last so that a failure here does not hide any other test."""
 import ctypes as C
 
 import numpy as np
@@ -25,7 +26,7 @@ def _params(lib, _lib, n, J, fov):
     return p
 
 
-def test_forward_noalloc_matches_forward_on_two_calls():
+def test_forward_noalloc_matches_forward_on_calls_in_a_row():
     ensure_built()
     import torch
     from paper_1301_1215_gb300 import _lib
@@ -33,7 +34,8 @@ def test_forward_noalloc_matches_forward_on_two_calls():
     lib = _lib.load()
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
-    for call, (n, J, fov, seed) in enumerate([(64, 4, 13, 31), (384, 10, 96, 32)]):
+    calls = [(64, 4, 13, 31), (64, 8, 16, 33), (64, 4, 16, 34), (384, 10, 96, 32), (384, 10, 96, 35)]
+    for call, (n, J, fov, seed) in enumerate(calls):
         rng = synth.rng_for(seed)
         x = torch.from_numpy(synth.random_complex((1 + J, n, n), rng).astype(np.complex64)).to(dev)
         mask = torch.from_numpy(synth.radial_mask(n, 13, 0.1 * call)).to(dev)
