@@ -60,7 +60,7 @@ typedef enum {
   NLINV_EINVAL = 1,      /* bad argument (null pointer, unsupported size, host pointer where a device one is due) */
   NLINV_ENOMEM = 2,      /* device memory for the context's workspace could not be allocated */
   NLINV_ECUDA = 3,       /* a CUDA runtime call failed; nlinv_last_error() has its message */
-  NLINV_EBREAKDOWN = 4,  /* CG met a non-finite |r|^2 or Re<p, A p>; the step was skipped (alpha = 0) */
+  NLINV_EBREAKDOWN = 4,  /* CG met a non-finite |r|^2 or Re<p, A p>; that solve stopped there (no further step) */
   NLINV_ETIMEOUT = 5     /* nlinv_wait() gave up before the context's queued work finished */
 } nlinv_status;
 
@@ -69,7 +69,8 @@ typedef struct {
   int n;             /* grid side (twice the image matrix, Sec. 3.2); see nlinv_supported_size() */
   int ncoils;        /* J >= 1 (virtual) coils */
   int newton_steps;  /* Gauss-Newton steps per reconstruction, 1..64 */
-  int cg_iters;      /* CG iterations per Newton step (a fixed count, no tolerance exit), >= 0 */
+  int cg_iters;      /* CG iterations per Newton step (a fixed count; stops earlier only at the rounding floor,
+                        see nlinv_cg_stops), >= 0 */
   double alpha0;     /* alpha_0 of Eq. 3 (> 0) */
   double alpha_q;    /* alpha_{n+1} = max(alpha_q alpha_n, alpha_min), 0 < alpha_q <= 1 */
   double alpha_min;  /* floor of alpha_n, >= 0 */
@@ -77,6 +78,9 @@ typedef struct {
   double sobolev_l;  /* l of the Sobolev weight, >= 0 (32) */
   int fov;           /* half-width of Omega in pixels, 1..n/2 (n/4 by default) */
   int use_graph;     /* 1: replay each reconstruction as one captured CUDA graph; 0: launch kernel by kernel */
+  int tensor_dft;    /* 1: the radix-16 DFT stages of the transforms run on the tensor cores in split-BF16 with
+                        three passes (an optional precision path beside the paper's complex single precision,
+                        Sec. 3.2); compiled for n = 256 and 512; not used by batches.  0 (default): FP32 stages */
 } nlinv_params;
 
 typedef struct nlinv_ctx nlinv_ctx;
@@ -86,7 +90,7 @@ typedef struct nlinv_ctx nlinv_ctx;
 NLINV_API int nlinv_supported_size(int n);
 
 /* Defaults for an n x n grid with ncoils coils: 7 Newton steps, 30 CG iterations, alpha_0 = 1, alpha_q = 1/2,
- * alpha_min = 0, a = 220, l = 32, fov = n/4, use_graph = 1.  EINVAL if p is NULL. */
+ * alpha_min = 0, a = 220, l = 32, fov = n/4, use_graph = 1, tensor_dft = 0.  EINVAL if p is NULL. */
 NLINV_API nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils);
 
 /* Creates a context on the current CUDA device: validates *params, allocates the device workspace (about
@@ -216,9 +220,13 @@ typedef struct {
 typedef struct nlinv_batch nlinv_batch;
 
 /* Creates a batch for nframes frames whose shapes are frames[i].n and frames[i].ncoils (the pointers are not used
- * here).  params supplies the solver schedule and the Sobolev weight (its n, ncoils, fov and use_graph are
- * ignored).  stream as for nlinv_create.  Allocates one workspace per frame and captures the whole batched
- * reconstruction as one CUDA graph.  Errors: EINVAL, ENOMEM, ECUDA (message via nlinv_last_error(NULL)). */
+ * here).  params supplies the solver schedule and the Sobolev weight (its n, ncoils, fov, use_graph and tensor_dft
+ * are ignored).  stream as for nlinv_create.  Allocates one workspace per frame and captures the whole batched
+ * reconstruction as one CUDA graph: per grid side, one persistent launch per pass (as many blocks as fit on the
+ * GPU at once, each looping over the work items of all frames of that side), the sides as parallel branches.  With
+ * the environment variable NLINV_BATCH_MULTI=1, the sides 128, 192, 256, 320 and 384 share one launch per pass
+ * instead (a kernel that dispatches on each work item's side; slower on GB300: the side bodies spill registers).
+ * Errors: EINVAL, ENOMEM, ECUDA (message via nlinv_last_error(NULL)). */
 NLINV_API nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const nlinv_frame_desc* frames,
                                           void* stream, nlinv_batch** out);
 
@@ -240,7 +248,8 @@ NLINV_API nlinv_status nlinv_batch_destroy(nlinv_batch* batch);
 NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
 
 /* Times the kernels of one CG iteration of Eq. 3 with CUDA events on the context's stream, on the workspace left
- * by the last nlinv_reconstruct (whose CG state it advances; x is not changed): each kernel is launched reps times
+ * by the last nlinv_reconstruct (whose CG state it advances -- a solve that had stopped at its rounding floor is
+ * marked running again, so that every kernel does its full work; x is not changed): each kernel is launched reps times
  * back to back between two events, so ms_out gets its steady-state launch duration (consecutive launches overlap
  * their ramp and drain, as the passes of a graph replay do).  With reps = 1 the six kernels run once each, in
  * order.  ms_out (HOST, 6 doubles) receives the mean duration in milliseconds of, in order:
@@ -275,22 +284,33 @@ NLINV_API nlinv_status nlinv_autotune(nlinv_ctx* ctx, const nlinv_c32* y, const 
  * graph was replayed).  -1 for a NULL context. */
 NLINV_API long nlinv_last_launch_count(const nlinv_ctx* ctx);
 
+/* Where the CG solves of the last reconstruction on ctx stopped (the CG steps of Eq. 3, Sec. 3.1).  CG runs
+ * params.cg_iters iterations; it stops earlier only at the rounding floor of its single-precision arithmetic --
+ * |r| <= 2^-24 |b| (the FP32 unit roundoff relative to the right-hand side b, which includes b = 0),
+ * Re<p, A p> <= 0 (impossible in exact arithmetic for the positive definite system of Eq. 3) or a non-finite
+ * value -- and the rest of that solve then leaves dx unchanged (its remaining CG launches return at once).  out (HOST, len >= newton_steps ints) receives per Newton step the index of
+ * the CG iteration that stopped, or -1 when all iterations ran.  Waits for the context's stream.  Errors: EINVAL
+ * (NULL or short out, no reconstruction yet), ECUDA. */
+NLINV_API nlinv_status nlinv_cg_stops(nlinv_ctx* ctx, int* out, int len);
+
 /* F x like nlinv_forward, but without a context and without allocating any device memory.  The paper has no
  * counterpart; it serves callers that may not allocate device memory when they apply F: a real-time loop that
  * reserves its GPU memory up front and must not see a cudaMalloc fail or stall mid-series, or a host framework
  * that owns every device allocation.  Such callers cannot use nlinv_create, whose workspace is allocated.
- * The scratch (the Omega-column transform buffer, the coil maps, the twiddle and Sobolev tables) lives in one
- * file-scope device array of 16 MiB that every GPU loading this library holds until the process exits; a call
- * whose n, ncoils and fov need more than that is rejected with EINVAL (384 x 384 with 10 coils and fov = n/4 fits;
- * 512 x 512 with 16 coils does not).  The caller passes x (1+J planes), mask and y_out (J planes), all device
- * pointers, and a cudaStream_t (NULL = legacy default stream); params supplies n, ncoils, fov, sobolev_a and
- * sobolev_l (the other fields are ignored).
- * The first call on a device finds the array's device address, and the first call, and every call whose n or
- * Sobolev parameters differ from the previous call's on that device, writes the tables and waits for the stream.
- * All calls on a device share the one array and every call overwrites it (nothing in it has to start at zero):
- * calls that overlap on the GPU -- on different streams or host threads -- race and give wrong results.
- * Errors: EINVAL (bad params, NULL or host pointers, sizes beyond the scratch), ECUDA; message via
- * nlinv_last_error(NULL). */
+ * The scratch (the twiddle and Sobolev tables at fixed offsets, then the Omega-column transform buffer and the
+ * coil maps) lives in one file-scope device array of 16 MiB that every GPU loading this library holds until the
+ * process exits; a call whose n, ncoils and fov need more than that is rejected with EINVAL (384 x 384 with 10
+ * coils and fov = n/4 fits; 512 x 512 with 16 coils does not).  The caller passes x (1+J planes), mask and y_out
+ * (J planes), device (or managed) memory of the current device, and a cudaStream_t (NULL = legacy default stream);
+ * params supplies n, ncoils, fov, sobolev_a and sobolev_l (the other fields are ignored).
+ * Set-up: the first call on a device (with that device current) finds the array's device address, and the first
+ * call, and every call whose n or Sobolev parameters differ from the previous call's on that device, writes the
+ * tables and waits for the stream -- so make such a call before any stream capture.  The device address and the
+ * record of the tables are kept for the process: do not call this after cudaDeviceReset.
+ * All calls on a device share the one array and every call overwrites its buffers (nothing in it has to start at
+ * zero): calls that overlap on the GPU -- on different streams or host threads -- race and give wrong results.
+ * Errors: EINVAL (bad params, NULL pointers, memory of another device or of the host, sizes beyond the scratch),
+ * ECUDA; message via nlinv_last_error(NULL). */
 NLINV_API nlinv_status nlinv_forward_noalloc(const nlinv_params* params, void* stream, const nlinv_c32* x,
                                              const uint8_t* mask, nlinv_c32* y_out);
 

@@ -22,7 +22,8 @@ class Params(C.Structure):
     """Mirror of nlinv_params."""
     _fields_ = [("n", _int), ("ncoils", _int), ("newton_steps", _int), ("cg_iters", _int),
                 ("alpha0", _dbl), ("alpha_q", _dbl), ("alpha_min", _dbl),
-                ("sobolev_a", _dbl), ("sobolev_l", _dbl), ("fov", _int), ("use_graph", _int)]
+                ("sobolev_a", _dbl), ("sobolev_l", _dbl), ("fov", _int), ("use_graph", _int),
+                ("tensor_dft", _int)]
 
 
 class Tuning(C.Structure):
@@ -57,6 +58,7 @@ SIGNATURES = {
     "nlinv_batch_launch_count": (_long, [_vp]),
     "nlinv_batch_destroy": (_int, [_vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
+    "nlinv_cg_stops": (_int, [_vp, C.POINTER(_int), _int]),
     "nlinv_gridder_create": (_int, [_int, _int, C.POINTER(_dbl), _vp, C.POINTER(_vp)]),
     "nlinv_grid": (_int, [_vp, _int, _vp, _vp, _vp]),
     "nlinv_gridder_destroy": (_int, [_vp]),

@@ -223,6 +223,13 @@ template <int A, int B> struct Split {
   static constexpr int SM_LANE_COL = SM_LANE + ((2 - SM_LANE % 16) + 16) % 16;
 };
 
+// Radix-16 register DFTs stay on the CUDA cores unless a tensor-core engine (tc_dft.cuh) is passed in.
+struct NoTc {
+  static constexpr bool enabled = false;
+  template <int D, int E>
+  __device__ __forceinline__ void dft16(float2 (&)[E], bool) {}
+};
+
 // Layout A(P1, P2) -> layout B(P1, P2) for one lane of P1*P2 points.
 //   v      register slots of this thread (v[0..P2) valid on entry if idx < P1; v[0..P1) valid on exit if idx < P2)
 //   sm     this lane's shared-memory exchange area (>= P2*(P1+1) float2)
@@ -232,12 +239,17 @@ template <int A, int B> struct Split {
 // General form: the threads of the two steps may be mapped differently onto the lanes (a lane's exchange area is
 // the same in both).  Step 1 runs on the threads with in_ok (index in_idx < P1 of the lane whose area is sm_in),
 // step 3 on those with out_ok (index out_idx < P2, area sm_out).
-template <int P1, int P2, int D, int E>
+// tc: with an enabled tensor-core engine, a radix-16 register DFT (step 1 when P2 = 16, step 3 when P1 = 16) runs
+// as one block-wide tensor-core contraction instead (every thread takes part; threads without data pass zeros).
+template <int P1, int P2, int D, int E, class TC = NoTc>
 __device__ __forceinline__ void fft_AtoB2(float2 (&v)[E], float2* sm_in, int in_idx, bool in_ok, float2* sm_out,
-                                          int out_idx, bool out_ok, const float2* tw) {
+                                          int out_idx, bool out_ok, const float2* tw, TC* tc = nullptr) {
   constexpr int S = P1 + 1;
+  constexpr bool tc1 = TC::enabled && P2 == 16;
+  constexpr bool tc3 = TC::enabled && P1 == 16;
+  if constexpr (tc1) tc->template dft16<D>(v, in_ok);
   if (in_ok) {
-    RegDFT<P2, D>::run(v);
+    if constexpr (!tc1) RegDFT<P2, D>::run(v);
     static_for<P2>([&](auto kc) {
       constexpr int k2 = decltype(kc)::value;
       float2 w = tw[k2 * P1 + in_idx];
@@ -248,14 +260,15 @@ __device__ __forceinline__ void fft_AtoB2(float2 (&v)[E], float2* sm_in, int in_
   __syncthreads();
   if (out_ok) {
     static_for<P1>([&](auto nc) { constexpr int n1 = decltype(nc)::value; v[n1] = sm_out[out_idx * S + n1]; });
-    RegDFT<P1, D>::run(v);
+    if constexpr (!tc3) RegDFT<P1, D>::run(v);
   }
+  if constexpr (tc3) tc->template dft16<D>(v, out_ok);
   __syncthreads();
 }
 
-template <int P1, int P2, int D, int E>
-__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx) {
-  fft_AtoB2<P1, P2, D>(v, sm, idx, idx < P1, sm, idx, idx < P2, tw);
+template <int P1, int P2, int D, int E, class TC = NoTc>
+__device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx, TC* tc = nullptr) {
+  fft_AtoB2<P1, P2, D>(v, sm, idx, idx < P1, sm, idx, idx < P2, tw, tc);
 }
 
 }  // namespace nlv

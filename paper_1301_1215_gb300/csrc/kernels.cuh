@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include "fft_core.cuh"
+#include "tc_dft.cuh"
 
 namespace nlv {
 
@@ -27,15 +28,25 @@ constexpr int kMaxNewton = 64;
 // Scalars of the CG and Newton iterations, kept in device memory (FP64).
 struct Scalars {
   double rr;                     // |r|^2 of the current CG residual (numerator of alpha)
+  double rr0;                    // |b|^2 of the current CG solve (the reference of the rounding floor)
   double rr_prev;                // |r|^2 of the previous CG residual (denominator of the next beta)
   double alpha;                  // CG step length
   double beta;                   // CG direction update
   double pq;                     // last Re<p, A p>
   double last;                   // result of a RED_NONE reduction
   double resid[kMaxNewton + 1];  // |y - F x_n| per Newton step
-  int flags;                     // bit 0: CG breakdown (a non-finite |r|^2 or Re<p, A p>)
+  int cg_stop[kMaxNewton];       // per Newton step: the CG iteration that reached the rounding floor, -1 if none
+  int flags;                     // bit 0: CG breakdown (a non-finite |r|^2 or Re<p, A p>);
+                                 // bit 1: the current CG solve has reached the rounding floor (latched)
   unsigned ticket;               // completion counter of the last-block reduction
 };
+
+constexpr int kFlagBreakdown = 1;
+constexpr int kFlagCgStopped = 2;
+// Rounding floor of CG: the solve stops once |r|^2 <= kCgFloor2 |b|^2, i.e. |r| at the FP32 unit roundoff 2^-24
+// relative to |b| (further iterations cannot improve a single-precision solution; left to run, the recursive
+// residual decays into the FP32 denormal range, where the step lengths lose their precision).
+constexpr double kCgFloor2 = 0x1p-48;
 
 struct KArgs {
   int N, J, f, Wc;          // grid side, coils, half-width of Omega, compact width 2f
@@ -65,7 +76,8 @@ struct KArgs {
   double* partials;         // one double per block
   Scalars* sc;
   int reduce;               // Reduce
-  int slot;                 // RED_RESID index
+  int slot;                 // RED_RESID index; RED_RR_INIT and the CG step: the Newton step
+  int iter;                 // CG step: index of the CG iteration
   const float2* q;          // CG step: A p
   long n2;                  // vector passes: number of float4 (two complex values each)
   // Re<p, A p> without a last-block tail: the normal-operator pass of the CG iteration only writes one FP64
@@ -77,6 +89,8 @@ struct KArgs {
   double* rr_part;
   int n_rr;
   float coef;               // vector passes: second coefficient of out = alpha X + coef Y
+  const void* tcB;          // tensor-core passes: the B tiles of the radix-16 DFT stage (tc_dft.cuh)
+  int cgskip;               // a launch of the CG iteration: it returns at once when the solve has stopped
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -87,6 +101,21 @@ struct KArgs {
 __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// True for a launch of the CG iteration whose solve has stopped at its rounding floor (Scalars::flags, latched by
+// the CG step): the block then skips its work -- the stopped solve's remaining iterations are empty steps (the dx
+// they would leave is the one already there).  The flag can be set by block 0 of the CG step while other blocks of
+// that same launch start, so thread 0 reads it once for the whole block.  Every thread of the block must call this
+// (it contains barriers); A.cgskip is the same for the whole block.
+__device__ __forceinline__ bool cg_stopped(const KArgs& A) {
+  if (!A.cgskip) return false;
+  __shared__ int s_stop;
+  if (threadIdx.x == 0) s_stop = (*(volatile const int*)&A.sc->flags & kFlagCgStopped) != 0;
+  __syncthreads();
+  const bool stop = s_stop != 0;
+  __syncthreads();
+  return stop;
 }
 
 // ------------------------------------------------------------------------------------------- geometry ----
@@ -141,19 +170,25 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 __device__ __forceinline__ void finalize_scalar(Scalars* sc, int reduce, int slot, double total) {
   switch (reduce) {
     case RED_RESID: sc->resid[slot] = sqrt(total); break;
-    case RED_RR_INIT: sc->rr = total; sc->beta = 0.0; break;
+    case RED_RR_INIT:           // a new CG solve starts: nothing has stopped yet
+      sc->rr = total;
+      sc->rr0 = total;
+      sc->beta = 0.0;
+      sc->flags &= ~kFlagCgStopped;
+      sc->cg_stop[slot] = -1;
+      break;
     default: sc->last = total; break;
   }
 }
 
-// Every thread passes its FP32 partial; per-block sums in FP64 go to partials[], and the last block to finish
+// Every thread passes its partial; per-block sums in FP64 go to partials[], and the last block to finish
 // adds them in block order (so the result does not depend on scheduling) and updates the scalars.
 // bid / nblk: this block's index and the number of blocks working on the same problem (the whole grid, or one
 // frame's share of a batched grid).
-__device__ __forceinline__ void grid_reduce(float mine, const KArgs& A, int bid, int nblk) {
+__device__ __forceinline__ void grid_reduce(double mine, const KArgs& A, int bid, int nblk) {
   __shared__ double red[32];
   __shared__ bool last;
-  double s = block_sum((double)mine, red);
+  double s = block_sum(mine, red);
   if (threadIdx.x == 0) {
     A.partials[bid] = s;
     __threadfence();
@@ -251,8 +286,10 @@ constexpr int kRowCtasPerSM = 2;
 // plane after its rows, all of its threads working on it.  A thread takes two pixels per step (o and
 // o + blockDim.x) and issues every load of both before the first use; the coil sum of a pixel runs over even and
 // odd coils in two partial sums added at the end.
+// Dot-product partials: a thread sums at most 32 products in FP32 (one row round, or two pixels of the rho slice)
+// before adding them to its FP64 partial, so the FP32 summation length is bounded whatever the problem size.
 template <int N, int MODE, bool STDF>
-__device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
+__device__ __forceinline__ double rho_slice(const KArgs& A, int bid) {
   const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc, J = A.J;
   constexpr long plane = (long)N * N;
   const long e_begin = (long)bid * A.rho_per_cta;
@@ -260,8 +297,9 @@ __device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
   const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
   const size_t stride = (size_t)Wc * Wc;
   const long bd = blockDim.x;
-  float acc = 0.f;
+  double accd = 0.0;
   for (long o0 = e_begin + threadIdx.x; o0 < e_end; o0 += 2 * bd) {
+    float acc = 0.f;
     float2 a[2], b[2];
     const float2* zp[2];
     bool ok[2], om[2];
@@ -318,15 +356,17 @@ __device__ __forceinline__ float rho_slice(const KArgs& A, int bid) {
         acc += bb.x * bb.x + bb.y * bb.y;
       }
     }
+    accd += (double)acc;
   }
-  return acc;
+  return accd;
 }
 
 // Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
-template <int N1, int N2, int MODE, bool STDF = false>
-__device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw) {
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc>
+__device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw,
+                                              TC* tc = nullptr) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
   constexpr int N = S::N, TL = S::TL, E = S::E;
@@ -337,8 +377,10 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   const int laneA = threadIdx.x / N1, idxA = threadIdx.x % N1;
   const bool mapA = (int)threadIdx.x < LANES * N1;
   const int laneB = threadIdx.x / N2, idxB = threadIdx.x % N2;
+  const bool mapB = (int)threadIdx.x < LANES * N2;           // threads beyond the whole lanes stay idle
   const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc;
-  float acc = 0.f;
+  float acc = 0.f;        // this round's products (at most N1 <= 16 complex values per thread)
+  double accd = 0.0;      // FP64 sum of the rounds
   const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
   float2* smA = (float2*)(smem_raw + L.xch) + laneA * S::SM_LANE;
   float2* smB = (float2*)(smem_raw + L.xch) + laneB * S::SM_LANE;
@@ -353,7 +395,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
-  const bool activeA = mapA && RA < r_end, activeB = RB < r_end;
+  const bool activeA = mapA && RA < r_end, activeB = mapB && RB < r_end;
   const int e1A = RA % N;
   float2 v[E];
 
@@ -442,7 +484,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   }
 
   if constexpr (T::inverse_first) {
-    fft_AtoB2<N1, N2, +1>(v, smA, idxA, mapA, smB, idxB, true, twA);
+    fft_AtoB2<N1, N2, +1>(v, smA, idxA, mapA, smB, idxB, mapB, twA, tc);
     // layout B: thread b < N2 holds elements b + N2*m; keep the Omega columns
     if (activeB) {
 #pragma unroll
@@ -452,7 +494,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
       }
     }
   } else {
-    fft_AtoB2<N1, N2, -1>(v, smA, idxA, mapA, smB, idxB, true, twA);
+    fft_AtoB2<N1, N2, -1>(v, smA, idxA, mapA, smB, idxB, mapB, twA, tc);
     const unsigned char* smask = smem_raw + L.mask + (size_t)laneB * N;
     if constexpr (MODE == ROW_PSF) {
       {
@@ -462,7 +504,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
           v[m] = cscale(v[m], sc);
         }
       }
-      fft_AtoB2<N2, N1, +1>(v, smB, idxB, true, smA, idxA, mapA, twB);
+      fft_AtoB2<N2, N1, +1>(v, smB, idxB, mapB, smA, idxA, mapA, twB, tc);
       if (activeA) {
 #pragma unroll
         for (int m = 0; m < N2; ++m) {
@@ -523,16 +565,20 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
     }
   }
   __syncthreads();       // the next round restages the side rows
+  if constexpr (T::reduces) {
+    accd += (double)acc;
+    acc = 0.f;
+  }
   }  // rounds
 
-  if constexpr (T::has_rho) acc += rho_slice<N, MODE, STDF>(A, bid);
+  if constexpr (T::has_rho) accd += rho_slice<N, MODE, STDF>(A, bid);
   if constexpr (T::reduces) {
     if (MODE == ROW_FFT_W_NORMAL && A.pq_part) {
       __shared__ double red[32];
-      const double sblk = block_sum((double)acc, red);
+      const double sblk = block_sum(accd, red);
       if (threadIdx.x == 0) A.pq_part[bid] = sblk;
     } else {
-      grid_reduce(acc, A, bid, nblk);
+      grid_reduce(accd, A, bid, nblk);
     }
   }
 }
@@ -541,6 +587,7 @@ template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
+  if (cg_stopped(A)) return;
   row_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, gridDim.x, smem_raw);
 }
 
@@ -605,8 +652,8 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
   }
 }
 
-template <int N1, int N2, int MODE, bool STDF = false>
-__device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw) {
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc>
+__device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw, TC* tc = nullptr) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
@@ -664,7 +711,7 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
   __syncthreads();
 
   if constexpr (MODE == COL_PROD_FFT || MODE == COL_SIM_FFT) {
-    fft_AtoB<N1, N2, -1>(v, sm, twA, idx);
+    fft_AtoB<N1, N2, -1>(v, sm, twA, idx, tc);
     if (active && idx < N2) {
 #pragma unroll
       for (int m = 0; m < N1; ++m) {
@@ -674,7 +721,7 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
     }
     return;
   } else {
-    fft_AtoB<N1, N2, +1>(v, sm, twA, idx);
+    fft_AtoB<N1, N2, +1>(v, sm, twA, idx, tc);
     if constexpr (MODE == COL_IFFT_C) {
       if (active && idx < N2) {
 #pragma unroll
@@ -712,7 +759,7 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
           v[m] = out;
         }
       }
-      fft_AtoB<N2, N1, -1>(v, sm, twB, idx);
+      fft_AtoB<N2, N1, -1>(v, sm, twB, idx, tc);
       if (active && idx < N1) {
 #pragma unroll
         for (int m = 0; m < N2; ++m) {
@@ -728,7 +775,40 @@ template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
+  if (cg_stopped(A)) return;
   col_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, smem_raw);
+}
+
+// ------------------------------------------------------------------------------- tensor-core passes ----
+// The same passes with their radix-16 DFT stages on the tensor cores (tc_dft.cuh): the engine's shared memory
+// follows the pass's own layout (offset tc_offset(...) below), its TMEM is allocated after the dependent-launch
+// wait and freed at the end.
+__host__ __device__ constexpr size_t tc_offset(size_t pass_bytes) { return (pass_bytes + 127) / 128 * 128; }
+
+template <int N1, int N2, int MODE, bool STDF>
+__global__ void __launch_bounds__(kRowMaxThreads, 1) row_pass_tc(const KArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pdl_enter();
+  if (cg_stopped(A)) return;
+  using S = Split<N1, N2>;
+  const RowSmem L = row_smem(MODE, S::N, blockDim.x / S::TL, S::SM_LANE);
+  TcDft tc;
+  tc.setup(smem_raw + tc_offset(L.total), A.tcB, &A.sc->flags);
+  row_pass_body<N1, N2, MODE, STDF, TcDft>(A, blockIdx.x, gridDim.x, smem_raw, &tc);
+  tc.teardown();
+}
+
+template <int N1, int N2, int MODE, bool STDF>
+__global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS, 1) col_pass_tc(const KArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  pdl_enter();
+  if (cg_stopped(A)) return;
+  using S = Split<N1, N2>;
+  const ColSmem L = col_smem(MODE, S::N, ColCfg<N1, N2>::C, S::SM_LANE_COL, STDF ? S::N / 2 : A.Wc);
+  TcDft tc;
+  tc.setup(smem_raw + tc_offset(L.total), A.tcB, &A.sc->flags);
+  col_pass_body<N1, N2, MODE, STDF, TcDft>(A, blockIdx.x, smem_raw, &tc);
+  tc.teardown();
 }
 
 // --------------------------------------------------------------------------------------------- batches ----
@@ -739,12 +819,16 @@ struct BatchArgs {
   const KArgs* args;       // per-frame arguments (device)
   const int* first;        // nframes + 1 block offsets (device)
   int nframes;
+  int total;               // work items = first[nframes]; a block takes items blockIdx.x, + gridDim.x, ...
 };
 
-__device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int& bid, int& nblk) {
+// Work item w of a batched launch: its frame's arguments (copied to shared memory), its block index within the
+// frame and the frame's block count.  Every thread of the block calls it (barriers).
+__device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int w, int& bid, int& nblk) {
   __shared__ KArgs sa;
   __shared__ int sf, sb, sn;
-  // the frame is the number of block offsets first[1 .. nframes-1] at or below this block (offsets increase):
+  __syncthreads();         // the previous work item of this block is done with sa
+  // the frame is the number of block offsets first[1 .. nframes-1] at or below this item (offsets increase):
   // the first warp tests 32 of them per step, all loads of a step in flight together
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x, nl = warp_lanes();
@@ -752,12 +836,12 @@ __device__ __forceinline__ const KArgs& batch_frame(const BatchArgs& B, int& bid
     int f = 0;
     for (int base = 1; base < B.nframes; base += nl) {
       const int k = base + lane;
-      const bool le = lane < nl && k < B.nframes && B.first[k] <= (int)blockIdx.x;
+      const bool le = lane < nl && k < B.nframes && B.first[k] <= w;
       f += __popc(__ballot_sync(live, le));
     }
     if (lane == 0) {
       sf = f;
-      sb = (int)blockIdx.x - B.first[f];
+      sb = w - B.first[f];
       sn = B.first[f + 1] - B.first[f];
     }
   }
@@ -774,19 +858,103 @@ template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
-  int bid, nblk;
-  const KArgs& A = batch_frame(B, bid, nblk);
-  row_pass_body<N1, N2, MODE, STDF>(A, bid, nblk, smem_raw);
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = batch_frame(B, w, bid, nblk);
+    if (cg_stopped(A)) continue;
+    row_pass_body<N1, N2, MODE, STDF>(A, bid, nblk, smem_raw);
+  }
 }
 
 template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass_batch(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
-  int bid, nblk;
-  const KArgs& A = batch_frame(B, bid, nblk);
-  col_pass_body<N1, N2, MODE, STDF>(A, bid, smem_raw);
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = batch_frame(B, w, bid, nblk);
+    if (cg_stopped(A)) continue;
+    col_pass_body<N1, N2, MODE, STDF>(A, bid, smem_raw);
+  }
 }
+
+// ------------------------------------------------------------------------- batches of several sides ----
+// One launch per pass for frames of every grid side in kMultiSides: the block dispatches on its work item's grid
+// side to that side's pass body.  Row passes run kRowMaxThreads threads (kRowMaxThreads / TL whole lanes of the
+// side, the rest idle), column passes kMultiColThreads (NLV_COL_C columns x the largest lane width).
+constexpr int kMultiSides[] = {128, 192, 256, 320, 384};
+constexpr int kNumMultiSides = 5;
+constexpr int kMultiColThreads = NLV_COL_C * 24;
+__host__ __device__ constexpr bool multi_side(int n) {
+  return n == 128 || n == 192 || n == 256 || n == 320 || n == 384;
+}
+
+// Each side's body is a separate (not inlined) function, so that registers are allocated per side rather than
+// across all sides' branches at once.
+template <int N1, int N2, int MODE, bool STDF>
+__device__ __noinline__ void row_body_call(const KArgs& A, int bid, int nblk, unsigned char* smem) {
+  row_pass_body<N1, N2, MODE, STDF>(A, bid, nblk, smem);
+}
+template <int N1, int N2, int MODE, bool STDF>
+__device__ __noinline__ void col_body_call(const KArgs& A, int bid, unsigned char* smem) {
+  col_pass_body<N1, N2, MODE, STDF>(A, bid, smem);
+}
+template <int MODE, bool STDF>
+__device__ __forceinline__ void row_body_of_side(const KArgs& A, int bid, int nblk, unsigned char* smem) {
+  switch (A.N) {
+    case 128: row_body_call<8, 16, MODE, STDF>(A, bid, nblk, smem); break;
+    case 192: row_body_call<12, 16, MODE, STDF>(A, bid, nblk, smem); break;
+    case 256: row_body_call<16, 16, MODE, STDF>(A, bid, nblk, smem); break;
+    case 320: row_body_call<16, 20, MODE, STDF>(A, bid, nblk, smem); break;
+    default: row_body_call<16, 24, MODE, STDF>(A, bid, nblk, smem); break;
+  }
+}
+template <int MODE, bool STDF>
+__device__ __forceinline__ void col_body_of_side(const KArgs& A, int bid, unsigned char* smem) {
+  switch (A.N) {
+    case 128: col_body_call<8, 16, MODE, STDF>(A, bid, smem); break;
+    case 192: col_body_call<12, 16, MODE, STDF>(A, bid, smem); break;
+    case 256: col_body_call<16, 16, MODE, STDF>(A, bid, smem); break;
+    case 320: col_body_call<16, 20, MODE, STDF>(A, bid, smem); break;
+    default: col_body_call<16, 24, MODE, STDF>(A, bid, smem); break;
+  }
+}
+
+template <int MODE, bool STDF>
+__global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass_multi(const BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = batch_frame(B, w, bid, nblk);
+    if (cg_stopped(A)) continue;
+    row_body_of_side<MODE, STDF>(A, bid, nblk, smem_raw);
+  }
+}
+
+template <int MODE, bool STDF>
+__global__ void __launch_bounds__(kMultiColThreads) col_pass_multi(const BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_enter();
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = batch_frame(B, w, bid, nblk);
+    if (cg_stopped(A)) continue;
+    col_body_of_side<MODE, STDF>(A, bid, smem_raw);
+  }
+}
+
+// The multi-side kernels of every pass (defined in batch_multi.cu) and their dynamic shared memory (the largest
+// over the sides).
+struct MultiKernels {
+  const void* row[NUM_ROW_MODES];
+  const void* row_std[NUM_ROW_MODES];
+  const void* col[NUM_COL_MODES];
+  const void* col_std[NUM_COL_MODES];
+  size_t row_smem[NUM_ROW_MODES];
+  size_t col_smem[NUM_COL_MODES];
+};
+const MultiKernels* multi_kernels();
 
 // ------------------------------------------------------------------------------- per-size kernel table ----
 struct SizeKernels {
@@ -805,8 +973,16 @@ struct SizeKernels {
   const void* col_std[NUM_COL_MODES];
   const void* row_std_batch[NUM_ROW_MODES];
   const void* col_std_batch[NUM_COL_MODES];
+  // Passes with their radix-16 DFT stages on the tensor cores (sides whose split has a factor 16); nullptr where
+  // not compiled.  row_tc_std / col_tc_std: the standard-field-of-view forms, as row_std / col_std.
+  const void* row_tc[NUM_ROW_MODES];
+  const void* col_tc[NUM_COL_MODES];
+  const void* row_tc_std[NUM_ROW_MODES];
+  const void* col_tc_std[NUM_COL_MODES];
   size_t row_smem(int mode, int lanes) const { return nlv::row_smem(mode, N1 * N2, lanes, sm_lane).total; }
   size_t col_smem(int mode, int Wc) const { return nlv::col_smem(mode, N1 * N2, col_lanes, sm_lane_col, Wc).total; }
+  size_t row_smem_tc(int mode, int lanes) const { return tc_offset(row_smem(mode, lanes)) + tc_smem_bytes(lanes * tl); }
+  size_t col_smem_tc(int mode, int Wc) const { return tc_offset(col_smem(mode, Wc)) + tc_smem_bytes(col_threads); }
 };
 
 // Launch geometry of a row pass: `blocks` blocks of `lanes` lanes, each taking rows_per_cta rows (and rho_per_cta
@@ -871,6 +1047,29 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.row_std_batch[ROW_PSF] = (const void*)row_pass_batch<N1, N2, ROW_PSF, true>;
   s.row_std_batch[ROW_FFT_W_NORMAL] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_NORMAL, true>;
   s.col_std_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT, true>;
+  return s;
+}
+
+// The kernel table of a side whose split has a factor 16, with the tensor-core passes added.
+template <int N1, int N2> SizeKernels make_size_kernels_tc() {
+  static_assert(N1 == 16 || N2 == 16, "the tensor-core stage is a radix-16 DFT");
+  SizeKernels s = make_size_kernels<N1, N2>();
+  s.row_tc[ROW_W_IFFT] = (const void*)row_pass_tc<N1, N2, ROW_W_IFFT, false>;
+  s.row_tc[ROW_PSF] = (const void*)row_pass_tc<N1, N2, ROW_PSF, false>;
+  s.row_tc[ROW_FFT_P_OUT] = (const void*)row_pass_tc<N1, N2, ROW_FFT_P_OUT, false>;
+  s.row_tc[ROW_FFT_RESID] = (const void*)row_pass_tc<N1, N2, ROW_FFT_RESID, false>;
+  s.row_tc[ROW_P_IFFT] = (const void*)row_pass_tc<N1, N2, ROW_P_IFFT, false>;
+  s.row_tc[ROW_FFT_W_ADJ] = (const void*)row_pass_tc<N1, N2, ROW_FFT_W_ADJ, false>;
+  s.row_tc[ROW_FFT_W_NORMAL] = (const void*)row_pass_tc<N1, N2, ROW_FFT_W_NORMAL, false>;
+  s.row_tc[ROW_FFT_W_RHS] = (const void*)row_pass_tc<N1, N2, ROW_FFT_W_RHS, false>;
+  s.col_tc[COL_IFFT_C] = (const void*)col_pass_tc<N1, N2, COL_IFFT_C, false>;
+  s.col_tc[COL_PROD_FFT] = (const void*)col_pass_tc<N1, N2, COL_PROD_FFT, false>;
+  s.col_tc[COL_SIM_FFT] = (const void*)col_pass_tc<N1, N2, COL_SIM_FFT, false>;
+  s.col_tc[COL_IFFT_PROD_FFT] = (const void*)col_pass_tc<N1, N2, COL_IFFT_PROD_FFT, false>;
+  s.col_tc[COL_IFFT_ADJ_FFT] = (const void*)col_pass_tc<N1, N2, COL_IFFT_ADJ_FFT, false>;
+  s.row_tc_std[ROW_PSF] = (const void*)row_pass_tc<N1, N2, ROW_PSF, true>;
+  s.row_tc_std[ROW_FFT_W_NORMAL] = (const void*)row_pass_tc<N1, N2, ROW_FFT_W_NORMAL, true>;
+  s.col_tc_std[COL_IFFT_PROD_FFT] = (const void*)col_pass_tc<N1, N2, COL_IFFT_PROD_FFT, true>;
   return s;
 }
 

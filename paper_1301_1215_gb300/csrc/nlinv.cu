@@ -38,6 +38,7 @@ thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
 // dx += alpha p; r -= alpha q; partial of |r|^2 -> rr_part[bid], over this block's share of the A.n2 float4.
+// A thread sums the squares of at most two float4 (8 products) in FP32 before adding them to its FP64 partial.
 __device__ __forceinline__ void cg_step_update(float4& d, float4& r, const float4& p, const float4& q, float a,
                                                float& acc) {
   d.x = fmaf(a, p.x, d.x); d.y = fmaf(a, p.y, d.y); d.z = fmaf(a, p.z, d.z); d.w = fmaf(a, p.w, d.w);
@@ -52,8 +53,12 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
   float4* __restrict__ dx4 = (float4*)A.dx;
   // Two groups of operands per thread in flight: the first two are loaded while the block forms
   // alpha = |r|^2 / Re<p, A p> from the partials of the normal-operator pass (every block sums them in the same
-  // fixed order).  The system of Eq. 3 is positive definite, so Re<p, A p> <= 0 or |r|^2 = 0 only occurs once CG
-  // has reached the rounding floor: the step is then empty (alpha = 0).  Non-finite values set the breakdown flag.
+  // fixed order).  The solve stops at the rounding floor: |r|^2 <= kCgFloor2 |b|^2 (|r| at the FP32 unit roundoff
+  // relative to |b|, including b = 0), Re<p, A p> <= 0 (impossible in exact arithmetic for the positive definite
+  // system of Eq. 3) or a non-finite value.  This step and every later step of the same solve are then empty
+  // (alpha = 0), through a flag latched in the scalars until the next right-hand side, and block 0 records the
+  // iteration.  Non-finite values also set the breakdown flag.  Every block takes the same decision from the same
+  // partials, so a block that already sees the flag set by block 0 in this launch decides as block 0 did.
   const long stride = (long)nblk * blockDim.x;
   long i = bid * (long)blockDim.x + threadIdx.x;
   float4 p0, q0, r0, d0, p1, q1, r1, d1;
@@ -66,19 +71,36 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
   t = nlv::block_sum(t, red);
   if (threadIdx.x == 0) {
     const double rr = A.sc->rr;
+    const int flags = *(volatile int*)&A.sc->flags;
+    const bool was_stopped = (flags & nlv::kFlagCgStopped) != 0;
     double a = 0.0;
-    if (!isfinite(t) || !isfinite(rr)) {
-      if (bid == 0) A.sc->flags |= 1;
-    } else if (rr != 0.0 && t > 0.0) {
-      a = rr / t;
+    bool stop = false;
+    if (!was_stopped) {
+      if (!isfinite(t) || !isfinite(rr)) {
+        if (bid == 0) A.sc->flags |= nlv::kFlagBreakdown;
+        stop = true;
+      } else if (rr > nlv::kCgFloor2 * A.sc->rr0 && t > 0.0) {
+        a = rr / t;
+      } else {
+        stop = true;
+      }
     }
-    if (bid == 0) { A.sc->pq = t; A.sc->alpha = a; A.sc->rr_prev = rr; }
+    if (bid == 0) {
+      A.sc->pq = t;
+      A.sc->alpha = a;
+      A.sc->rr_prev = rr;
+      if (stop) {
+        A.sc->flags |= nlv::kFlagCgStopped;
+        A.sc->cg_stop[A.slot] = A.iter;
+      }
+    }
     s_alpha = (float)a;
   }
   __syncthreads();
   const float a = s_alpha;
-  float acc = 0.f;
+  double accd = 0.0;
   while (i < A.n2) {
+    float acc = 0.f;
     cg_step_update(d0, r0, p0, q0, a, acc);
     dx4[i] = d0;
     r4[i] = r0;
@@ -88,11 +110,12 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
       dx4[i1] = d1;
       r4[i1] = r1;
     }
+    accd += (double)acc;
     i += 2 * stride;
     if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
     if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
   }
-  const double s = nlv::block_sum((double)acc, red);
+  const double s = nlv::block_sum(accd, red);
   if (threadIdx.x == 0) A.rr_part[bid] = s;
 }
 
@@ -127,6 +150,7 @@ __global__ void image_kernel(const KArgs A) {
 
 __global__ void cg_step_kernel(const KArgs A) {
   nlv::pdl_enter();
+  if (nlv::cg_stopped(A)) return;
   cg_step_body(A, blockIdx.x, gridDim.x);
 }
 __global__ void add_kernel(const KArgs A) {
@@ -153,28 +177,33 @@ __global__ void cg_init_kernel(const KArgs A) {
   float4* __restrict__ r4 = (float4*)A.r;
   float4* __restrict__ p4 = (float4*)A.pout;
   float4* __restrict__ d4 = (float4*)A.dx;
-  float acc = 0.f;
+  double acc = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < A.n2; i += (long)gridDim.x * blockDim.x) {
     const float4 b = b4[i];
     r4[i] = b;
     p4[i] = b;
     d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    acc += b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w;
+    acc += (double)(b.x * b.x + b.y * b.y + b.z * b.z + b.w * b.w);
   }
   nlv::grid_reduce(acc, A, blockIdx.x, gridDim.x);
 }
 
 __global__ void cg_step_batch(const nlv::BatchArgs B) {
   nlv::pdl_enter();
-  int bid, nblk;
-  const KArgs& A = nlv::batch_frame(B, bid, nblk);
-  cg_step_body(A, bid, nblk);
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = nlv::batch_frame(B, w, bid, nblk);
+    if (nlv::cg_stopped(A)) continue;
+    cg_step_body(A, bid, nblk);
+  }
 }
 __global__ void add_batch(const nlv::BatchArgs B) {
   nlv::pdl_enter();
-  int bid, nblk;
-  const KArgs& A = nlv::batch_frame(B, bid, nblk);
-  add_body(A, bid, nblk);
+  for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
+    int bid, nblk;
+    const KArgs& A = nlv::batch_frame(B, w, bid, nblk);
+    add_body(A, bid, nblk);
+  }
 }
 
 constexpr int kVecThreads = 256;
@@ -230,6 +259,8 @@ struct nlinv_ctx {
   std::vector<Rec>* rec = nullptr;   // non-null: launches are recorded instead of issued
   bool pdl = true;            // programmatic dependent launches (NLINV_PDL=0 turns them off)
   bool std_fov = false;       // fov = N/4: the passes specialised for it (SizeKernels::row_std, col_std) apply
+  bool tc = false;            // radix-16 DFT stages on the tensor cores (params.tensor_dft)
+  void* tcB = nullptr;        // their B tiles (workspace)
   double last_alpha = 0.0;    // alpha_n of the last Newton step
   float2* ckpt = nullptr;     // non-null: q_reconstruct writes x_0 .. x_N here (nlinv_reconstruct_checkpoints)
   void* vjp_base = nullptr;   // scratch of nlinv_reconstruct_vjp (allocated on first use)
@@ -272,6 +303,7 @@ KArgs base_args(const nlinv_ctx* c) {
   a.partials = c->partials;
   a.sc = c->sc;
   a.reduce = nlv::RED_NONE;
+  a.tcB = c->tcB;
   return a;
 }
 
@@ -285,7 +317,11 @@ nlv::RowGrid row_geom(const nlinv_ctx* c, bool with_rho) {
     g.rho_per_cta = with_rho ? (int)((c->plane + g.blocks - 1) / g.blocks) : 0;
     return g;
   }
-  return nlv::row_grid(c->k, c->J * c->N, with_rho ? c->plane : 0, c->sms, c->row_ctas_per_sm);
+  nlv::RowGrid g = nlv::row_grid(c->k, c->J * c->N, with_rho ? c->plane : 0, c->sms, c->row_ctas_per_sm);
+  // tensor-core passes: whole warps (every lane of a warp takes part in tcgen05.ld), the extra lanes idle
+  if (c->tc)
+    while ((g.lanes * c->k->tl) % 32 != 0) ++g.lanes;
+  return g;
 }
 
 int col_blocks(const nlinv_ctx* c) {
@@ -322,6 +358,10 @@ cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
   a.rows_per_cta = g.rows_per_cta;
   a.rho_per_cta = g.rho_per_cta;
   void* args[] = {&a};
+  if (c->tc) {
+    const void* fn = (c->std_fov && c->k->row_tc_std[mode]) ? c->k->row_tc_std[mode] : c->k->row_tc[mode];
+    return launch(c, fn, g.blocks, g.lanes * c->k->tl, c->k->row_smem_tc(mode, g.lanes), args);
+  }
   const void* fn = (c->std_fov && c->k->row_std[mode]) ? c->k->row_std[mode] : c->k->row[mode];
   return launch(c, fn, g.blocks, g.lanes * c->k->tl, c->k->row_smem(mode, g.lanes), args);
 }
@@ -329,6 +369,10 @@ cudaError_t row(nlinv_ctx* c, int mode, KArgs a) {
 cudaError_t col(nlinv_ctx* c, int mode, KArgs a) {
   a.nrows = c->J;
   void* args[] = {&a};
+  if (c->tc) {
+    const void* fn = (c->std_fov && c->k->col_tc_std[mode]) ? c->k->col_tc_std[mode] : c->k->col_tc[mode];
+    return launch(c, fn, col_blocks(c), c->k->col_threads, c->k->col_smem_tc(mode, c->Wc), args);
+  }
   const void* fn = (c->std_fov && c->k->col_std[mode]) ? c->k->col_std[mode] : c->k->col[mode];
   return launch(c, fn, col_blocks(c), c->k->col_threads, c->k->col_smem(mode, c->Wc), args);
 }
@@ -371,9 +415,11 @@ cudaError_t q_dir(nlinv_ctx* c, const float2* x, const float2* d) {
   return col(c, nlv::COL_IFFT_PROD_FFT, a);
 }
 
-// T <- FFT_col(conj(rho) z_j), zsum_j <- conj(c_j) z_j, with z_j = M FFT^-1_col(T)
-cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
+// T <- FFT_col(conj(rho) z_j), zsum_j <- conj(c_j) z_j, with z_j = M FFT^-1_col(T).  in_cg: a launch of the CG
+// iteration (skipped once the solve has stopped).
+cudaError_t q_adj_col(nlinv_ctx* c, const float2* x, bool in_cg = false) {
   KArgs a = base_args(c);
+  a.cgskip = in_cg ? 1 : 0;
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -382,9 +428,13 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
-// dx += alpha p, r -= alpha q, partials of |r|^2; alpha from the n_pq partials of the normal-operator pass
-cudaError_t q_cg_step(nlinv_ctx* c, int n_pq) {
+// dx += alpha p, r -= alpha q, partials of |r|^2; alpha from the n_pq partials of the normal-operator pass.
+// newton / iter: indices of the Newton step and of the CG iteration (recorded if the solve stops here).
+cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter) {
   KArgs a = base_args(c);
+  a.cgskip = 1;
+  a.slot = newton;
+  a.iter = iter;
   a.pq_part = c->pq_part;
   a.n_pq = n_pq;
   a.rr_part = c->rr_part;
@@ -416,6 +466,7 @@ cudaError_t q_add(nlinv_ctx* c) {
 // The steps are separate functions so that nlinv_profile_cg times exactly what a reconstruction launches.
 cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
   KArgs a = base_args(c);
+  a.cgskip = 1;
   a.src = c->p + c->plane;
   a.r = c->r + c->plane;
   a.pupd = 1;
@@ -429,6 +480,7 @@ cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
 
 cudaError_t q_cg_k2(nlinv_ctx* c, const float2* x) {
   KArgs a = base_args(c);
+  a.cgskip = 1;
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -441,6 +493,7 @@ cudaError_t q_cg_k2(nlinv_ctx* c, const float2* x) {
 
 cudaError_t q_cg_k3(nlinv_ctx* c) {
   KArgs a = base_args(c);
+  a.cgskip = 1;
   a.src = c->T;
   a.dst = c->T;
   a.mask = c->mask;
@@ -449,6 +502,7 @@ cudaError_t q_cg_k3(nlinv_ctx* c) {
 
 cudaError_t q_cg_k5(nlinv_ctx* c, float alpha) {
   KArgs a = base_args(c);
+  a.cgskip = 1;
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
@@ -460,14 +514,14 @@ cudaError_t q_cg_k5(nlinv_ctx* c, float alpha) {
   return row(c, nlv::ROW_FFT_W_NORMAL, a);
 }
 
-cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, bool first) {
+cudaError_t q_cg_iter(nlinv_ctx* c, const float2* x, float alpha, int newton, int iter) {
   cudaError_t e;
-  if ((e = q_cg_k1(c, first)) != cudaSuccess) return e;
+  if ((e = q_cg_k1(c, iter == 0)) != cudaSuccess) return e;
   if ((e = q_cg_k2(c, x)) != cudaSuccess) return e;
   if ((e = q_cg_k3(c)) != cudaSuccess) return e;
-  if ((e = q_adj_col(c, x)) != cudaSuccess) return e;
+  if ((e = q_adj_col(c, x, true)) != cudaSuccess) return e;
   if ((e = q_cg_k5(c, alpha)) != cudaSuccess) return e;
-  return q_cg_step(c, row_geom(c, true).blocks);
+  return q_cg_step(c, row_geom(c, true).blocks, newton, iter);
 }
 
 // Coil maps of c->x and the Newton residual r0 = y - F x with |r0| into resid[slot].
@@ -554,9 +608,10 @@ cudaError_t q_reconstruct(nlinv_ctx* c) {
     a.dx = c->dx;
     a.alpha = al;
     a.reduce = nlv::RED_RR_INIT;
+    a.slot = n;
     if ((e = row(c, nlv::ROW_FFT_W_RHS, a)) != cudaSuccess) return e;
     for (int i = 0; i < P.cg_iters; ++i)
-      if ((e = q_cg_iter(c, c->x, al, i == 0)) != cudaSuccess) return e;
+      if ((e = q_cg_iter(c, c->x, al, n, i)) != cudaSuccess) return e;
     if ((e = q_add(c)) != cudaSuccess) return e;
     if (c->ckpt &&
         (e = cudaMemcpyAsync(c->ckpt + (size_t)(n + 1) * c->vec, c->x, vb, cudaMemcpyDeviceToDevice, c->stream)) !=
@@ -595,6 +650,11 @@ nlinv_status validate(const nlinv_params* p, std::string* why) {
   if (!(p->sobolev_a >= 0) || !std::isfinite(p->sobolev_a)) { *why = "sobolev_a must be >= 0"; return NLINV_EINVAL; }
   if (!(p->sobolev_l >= 0) || !std::isfinite(p->sobolev_l)) { *why = "sobolev_l must be >= 0"; return NLINV_EINVAL; }
   if (p->fov < 1 || p->fov > p->n / 2) { *why = "fov must be in 1..n/2"; return NLINV_EINVAL; }
+  if (p->tensor_dft != 0 && p->tensor_dft != 1) { *why = "tensor_dft must be 0 or 1"; return NLINV_EINVAL; }
+  if (p->tensor_dft && !nlv::find_size(p->n)->row_tc[0]) {
+    *why = "tensor-core DFT stages are compiled for n = 256 and 512 only";
+    return NLINV_EINVAL;
+  }
   return NLINV_OK;
 }
 
@@ -624,6 +684,7 @@ nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils) {
   p->sobolev_l = 32.0;
   p->fov = n / 4;
   p->use_graph = 1;
+  p->tensor_dft = 0;
   return NLINV_OK;
 }
 
@@ -646,6 +707,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->f = params->fov;
   c->Wc = 2 * params->fov;
   c->std_fov = 4 * params->fov == params->n;
+  c->tc = params->tensor_dft != 0;
   c->plane = (long)c->N * c->N;
   c->vec = (long)(1 + c->J) * c->plane;
   c->k = nlv::find_size(c->N);
@@ -697,6 +759,16 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
     if (smem_err.empty() && c->k->col_std[m]) allow(c->k->col_std[m], c->k->col_smem(m, c->Wc));
     if (smem_err.empty() && c->k->col_std_batch[m]) allow(c->k->col_std_batch[m], c->k->col_smem(m, c->Wc));
   }
+  if (c->tc) {
+    for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) {
+      if (c->k->row_tc[m]) allow(c->k->row_tc[m], c->k->row_smem_tc(m, lanes_max));
+      if (smem_err.empty() && c->k->row_tc_std[m]) allow(c->k->row_tc_std[m], c->k->row_smem_tc(m, lanes_max));
+    }
+    for (int m = 0; m < nlv::NUM_COL_MODES && smem_err.empty(); ++m) {
+      if (c->k->col_tc[m]) allow(c->k->col_tc[m], c->k->col_smem_tc(m, c->Wc));
+      if (smem_err.empty() && c->k->col_tc_std[m]) allow(c->k->col_tc_std[m], c->k->col_smem_tc(m, c->Wc));
+    }
+  }
   if (!smem_err.empty()) {
     cudaGetLastError();
     g_create_error = smem_err;
@@ -717,7 +789,8 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   const int max_blocks = std::max(row_geom(c, true).blocks, std::max(c->vec_blocks, c->sms * kTuneVecMax));
   const size_t partb = align_up((size_t)max_blocks * sizeof(double), 256);
   const size_t scb = align_up(sizeof(Scalars), 256);
-  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 3 * partb + scb;
+  const size_t tcb = c->tc ? align_up(nlv::kTcBBytes, 256) : 0;
+  const size_t total = 6 * vecb + 2 * datab + Tb + 2 * cb + 2 * twb + wb + maskb + 3 * partb + scb + tcb;
   // NLINV_TEST_FAIL_ALLOC=1 (tests only): the workspace allocation reports out-of-memory without trying, so that
   // the ENOMEM path can be exercised without exhausting a GPU.
   const char* fail_alloc = std::getenv("NLINV_TEST_FAIL_ALLOC");
@@ -751,6 +824,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->pq_part = (double*)take(partb);
   c->rr_part = (double*)take(partb);
   c->sc = (Scalars*)take(scb);
+  if (c->tc) c->tcB = take(tcb);
 
   // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
   const int N = c->N, N1 = c->k->N1, N2 = c->k->N2;
@@ -776,6 +850,11 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   if (e == cudaSuccess) e = cudaMemcpy(c->twA, ta.data(), N * cplx, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->twB, tb.data(), N * cplx, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->wtab, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->tc) {
+    std::vector<uint16_t> bt(nlv::kTcBBytes / 2);
+    nlv::host_tc_btables(bt.data());
+    e = cudaMemcpy(c->tcB, bt.data(), nlv::kTcBBytes, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     g_create_error = std::string("context set-up: ") + cudaGetErrorString(e);
@@ -963,6 +1042,11 @@ nlinv_status nlinv_reconstruct(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* 
     NLV_TRY(cudaStreamSynchronize(c->stream), "synchronize");
     if (resid)
       for (int n = 0; n <= c->prm.newton_steps; ++n) resid[n] = hs.resid[n];
+    if (hs.flags & nlv::kFlagTcTimeout) {
+      int zero = 0;
+      cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(c, NLINV_ECUDA, "a tensor-core DFT stage did not complete within its time limit");
+    }
     if (hs.flags & 1) {
       int zero = 0;
       cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
@@ -1101,10 +1185,11 @@ nlinv_status nlinv_reconstruct_vjp(nlinv_ctx* c, const nlinv_c32* y, const uint8
     if (e == cudaSuccess) {
       KArgs a = base_args(c);
       a.src = g; a.r = c->r; a.pout = c->p; a.dx = c->dx; a.n2 = c->vec / 2; a.reduce = nlv::RED_RR_INIT;
+      a.slot = k;
       void* args[] = {&a};
       e = launch(c, (const void*)cg_init_kernel, c->vec_blocks, kVecThreads, 0, args);
     }
-    for (int i = 0; i < P.cg_iters && e == cudaSuccess; ++i) e = q_cg_iter(c, c->x, alpha, i == 0);
+    for (int i = 0; i < P.cg_iters && e == cudaSuccess; ++i) e = q_cg_iter(c, c->x, alpha, k, i);
     // v = DF_x u; dL/dy += v; dL/dx_ref += alpha u
     if (e == cudaSuccess) e = q_dir(c, c->x, c->dx);
     if (e == cudaSuccess) {
@@ -1130,6 +1215,13 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   if (reps < 1 || !ms_out) return fail(c, NLINV_EINVAL, "reps must be >= 1 and ms_out non-NULL");
   if (!c->have_state) return fail(c, NLINV_EINVAL, "run nlinv_reconstruct before nlinv_profile_cg");
   constexpr int K = kProfileKernels;
+  // the kernels are timed doing their full work: a solve that stopped at its floor is marked running again
+  {
+    int flags = 0;
+    NLV_TRY(cudaMemcpy(&flags, &c->sc->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+    flags &= ~nlv::kFlagCgStopped;
+    NLV_TRY(cudaMemcpy(&c->sc->flags, &flags, sizeof(int), cudaMemcpyHostToDevice), "write flags");
+  }
   cudaEvent_t ev[2];
   for (int i = 0; i < 2; ++i) NLV_TRY(cudaEventCreate(&ev[i]), "event create");
   const float al = (float)c->last_alpha;
@@ -1140,9 +1232,9 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
       case 0: return q_cg_k1(c, false);
       case 1: return q_cg_k2(c, c->x);
       case 2: return q_cg_k3(c);
-      case 3: return q_adj_col(c, c->x);
+      case 3: return q_adj_col(c, c->x, true);
       case 4: return q_cg_k5(c, al);
-      default: return q_cg_step(c, row_geom(c, true).blocks);
+      default: return q_cg_step(c, row_geom(c, true).blocks, 0, 0);
     }
   };
   cudaError_t e = cudaSuccess;
@@ -1161,6 +1253,17 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
 }
 
 long nlinv_last_launch_count(const nlinv_ctx* c) { return c ? c->launches : -1; }
+
+nlinv_status nlinv_cg_stops(nlinv_ctx* c, int* out, int len) {
+  if (!c) return NLINV_EINVAL;
+  if (!out || len < c->prm.newton_steps) return fail(c, NLINV_EINVAL, "out must hold newton_steps entries");
+  if (!c->have_state) return fail(c, NLINV_EINVAL, "no reconstruction has run on this context");
+  Scalars hs{};
+  NLV_TRY(cudaMemcpyAsync(&hs, c->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, c->stream), "read scalars");
+  NLV_TRY(cudaStreamSynchronize(c->stream), "synchronize");
+  for (int n = 0; n < c->prm.newton_steps; ++n) out[n] = hs.cg_stop[n];
+  return NLINV_OK;
+}
 
 nlinv_status nlinv_autotune(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x0, int reps,
                             nlinv_tuning* out, nlinv_tuning* table, int table_len) {
@@ -1300,6 +1403,8 @@ struct nlinv_batch {
   std::vector<Launch> launches;
   cudaGraphExec_t graph = nullptr;
   bool pdl = true;
+  bool multi = false;                       // one launch per pass for all sides the multi-side kernels cover
+                                            // (NLINV_BATCH_MULTI=1; measured slower, see nlinv_batch_create)
 };
 
 namespace {
@@ -1319,7 +1424,25 @@ void batch_free(nlinv_batch* b) {
   delete b;
 }
 
-// The batched kernel that runs the single-frame pass fn for several frames.
+// The multi-side kernel (kernels.cuh, "batches of several sides") that runs the single-frame pass fn of side k for
+// frames of every side, and its dynamic shared memory; nullptr if fn is not a pass.
+const void* multi_kernel(const SizeKernels* k, const void* fn, size_t* smem) {
+  const nlv::MultiKernels* mk = nlv::multi_kernels();
+  for (int m = 0; m < nlv::NUM_ROW_MODES; ++m) {
+    if (fn == k->row[m]) { *smem = mk->row_smem[m]; return mk->row[m]; }
+    if (k->row_std[m] && fn == k->row_std[m]) { *smem = mk->row_smem[m]; return mk->row_std[m]; }
+  }
+  for (int m = 0; m < nlv::NUM_COL_MODES; ++m) {
+    if (fn == k->col[m]) { *smem = mk->col_smem[m]; return mk->col[m]; }
+    if (k->col_std[m] && fn == k->col_std[m]) { *smem = mk->col_smem[m]; return mk->col_std[m]; }
+  }
+  *smem = 0;
+  if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
+  if (fn == (const void*)add_kernel) return (const void*)add_batch;
+  return nullptr;
+}
+
+// The batched kernel that runs the single-frame pass fn for several frames of one side.
 const void* batched_kernel(const SizeKernels* k, const void* fn) {
   for (int m = 0; m < nlv::NUM_ROW_MODES; ++m) {
     if (fn == k->row[m]) return k->row_batch[m];
@@ -1354,6 +1477,7 @@ nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const n
   if (!b) return fail(nullptr, NLINV_ENOMEM, "host allocation failed");
   b->prm = *params;
   if (const char* v = std::getenv("NLINV_PDL")) b->pdl = std::strcmp(v, "0") != 0;
+  if (const char* v = std::getenv("NLINV_BATCH_MULTI")) b->multi = std::strcmp(v, "0") != 0;
   cudaError_t e = cudaSuccess;
   if (stream) {
     b->stream = (cudaStream_t)stream;
@@ -1370,20 +1494,27 @@ nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const n
     fp.ncoils = frames[i].ncoils;
     fp.fov = frames[i].n / 4;
     fp.use_graph = 0;
+    fp.tensor_dft = 0;        // batches run the FP32 transforms
     const SizeKernels* k = nlv::find_size(fp.n);
     if (!k) return batch_fail(b, NLINV_EINVAL, "frame " + std::to_string(i) + ": unsupported grid side");
     nlinv_ctx* c = nullptr;
     const nlinv_status st = create_ctx(&fp, b->stream, nlv::kRowMaxThreads / k->tl, &c);
     if (st != NLINV_OK) return batch_fail(b, st, "frame " + std::to_string(i) + ": " + g_create_error);
     b->frames.push_back(c);
+    // frames of the sides the multi-side kernels cover form one group (side key 0); other sides one group each
+    const int key = (b->multi && nlv::multi_side(fp.n)) ? 0 : fp.n;
     size_t g = 0;
-    while (g < sides.size() && sides[g] != fp.n) ++g;
+    while (g < sides.size() && sides[g] != key) ++g;
     if (g == sides.size()) {
-      sides.push_back(fp.n);
+      sides.push_back(key);
       b->groups.emplace_back();
     }
     b->groups[g].push_back(i);
   }
+  int sms = 1, dev = 0, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // the launch sequence of every frame, merged launch by launch within each group
   std::vector<std::vector<nlinv_ctx::Rec>> recs(nframes);
   for (int i = 0; i < nframes; ++i) {
@@ -1401,30 +1532,56 @@ nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const n
     const SizeKernels* k = b->frames[fr[0]]->k;
     for (int i : fr)
       if (recs[i].size() != L) return batch_fail(b, NLINV_EINVAL, "frames of one grid side differ in schedule");
+    const bool multi = sides[g] == 0;
     for (size_t l = 0; l < L; ++l) {
       nlinv_batch::Launch bl{};
       bl.group = (int)g;
-      bl.fn = batched_kernel(k, recs[fr[0]][l].fn);
-      bl.block = recs[fr[0]][l].block;
+      size_t msmem = 0;
+      bl.fn = multi ? multi_kernel(k, recs[fr[0]][l].fn, &msmem) : batched_kernel(k, recs[fr[0]][l].fn);
       if (!bl.fn) return batch_fail(b, NLINV_EINVAL, "internal: no batched form of a pass");
       size_t off = (host.size() + 15) / 16 * 16;
       host.resize(off + fr.size() * sizeof(KArgs));
       arg_off.push_back(off);
       std::vector<int> first(fr.size() + 1, 0);
+      bl.block = 0;
       for (size_t t = 0; t < fr.size(); ++t) {
         const nlinv_ctx::Rec& r = recs[fr[t]][l];
-        if (r.fn != recs[fr[0]][l].fn || r.block != bl.block)
-          return batch_fail(b, NLINV_EINVAL, "frames of one grid side differ in pass shapes");
+        size_t ms = 0;
+        const void* same = multi ? multi_kernel(b->frames[fr[t]]->k, r.fn, &ms) : batched_kernel(k, r.fn);
+        if (same != bl.fn || (!multi && r.block != recs[fr[0]][l].block))
+          return batch_fail(b, NLINV_EINVAL, "frames of one group differ in pass shapes");
         std::memcpy(host.data() + off + t * sizeof(KArgs), &r.args, sizeof(KArgs));
         first[t + 1] = first[t] + r.grid;
-        bl.smem = std::max(bl.smem, r.smem);
+        bl.smem = multi ? msmem : std::max(bl.smem, r.smem);
+        bl.block = std::max(bl.block, r.block);
       }
-      bl.grid = first.back();
+      if (multi) {   // the multi-side kernels run fixed block shapes
+        const nlv::MultiKernels* mk = nlv::multi_kernels();
+        bool is_col = false;
+        for (int m = 0; m < nlv::NUM_COL_MODES; ++m)
+          is_col = is_col || bl.fn == mk->col[m] || (mk->col_std[m] && bl.fn == mk->col_std[m]);
+        bool is_row = false;
+        for (int m = 0; m < nlv::NUM_ROW_MODES; ++m)
+          is_row = is_row || bl.fn == mk->row[m] || (mk->row_std[m] && bl.fn == mk->row_std[m]);
+        if (is_row) bl.block = nlv::kRowMaxThreads;
+        if (is_col) bl.block = nlv::kMultiColThreads;
+      }
+      // persistent blocks: as many as are resident at once, each looping over the work items
+      cudaFuncAttributes fa{};
+      if (cudaFuncGetAttributes(&fa, bl.fn) == cudaSuccess && bl.smem > 0)
+        cudaFuncSetAttribute(bl.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin - (int)fa.sharedSizeBytes);
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bl.fn, bl.block, bl.smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return batch_fail(b, NLINV_EINVAL, "a batched pass does not fit on a multiprocessor");
+      }
+      bl.grid = std::min(first.back(), occ * sms);
       off = (host.size() + 15) / 16 * 16;
       host.resize(off + first.size() * sizeof(int));
       std::memcpy(host.data() + off, first.data(), first.size() * sizeof(int));
       first_off.push_back(off);
       bl.args.nframes = (int)fr.size();
+      bl.args.total = first.back();
       b->launches.push_back(bl);
     }
   }

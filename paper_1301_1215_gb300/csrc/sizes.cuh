@@ -30,3 +30,9 @@ inline const SizeKernels* find_size(int n) {
     static const ::nlv::SizeKernels k = ::nlv::make_size_kernels<a, b>(); \
     return &k;                                                      \
   }
+// A side that also has the passes with tensor-core radix-16 stages.
+#define NLV_SIZE_CASE_TC(n, a, b)                                   \
+  case n: {                                                         \
+    static const ::nlv::SizeKernels k = ::nlv::make_size_kernels_tc<a, b>(); \
+    return &k;                                                      \
+  }

@@ -40,7 +40,7 @@ class Nlinv:
 
     def __init__(self, n: int, ncoils: int, *, newton_steps: int = 7, cg_iters: int = 30, alpha0: float = 1.0,
                  alpha_q: float = 0.5, alpha_min: float = 0.0, sobolev_a: float = 220.0, sobolev_l: float = 32.0,
-                 fov: Optional[int] = None, use_graph: bool = True, device=None):
+                 fov: Optional[int] = None, use_graph: bool = True, tensor_dft: bool = False, device=None):
         lib = _lib.load()
         if not torch.cuda.is_available():
             raise RuntimeError("Nlinv needs a CUDA device; there is no CPU implementation")
@@ -54,6 +54,7 @@ class Nlinv:
         p.sobolev_a, p.sobolev_l = float(sobolev_a), float(sobolev_l)
         p.fov = int(n // 4 if fov is None else fov)
         p.use_graph = 1 if use_graph else 0
+        p.tensor_dft = 1 if tensor_dft else 0
         self.params = p
         self.n, self.ncoils = int(n), int(ncoils)
         self._h = C.c_void_p()
@@ -280,6 +281,14 @@ class Nlinv:
     def last_launch_count(self) -> int:
         """Kernel launches queued by the last call (kernel nodes of the graph when one was replayed)."""
         return int(self._lib.nlinv_last_launch_count(self._h))
+
+    def cg_stops(self) -> list:
+        """Per Newton step of the last reconstruction: the CG iteration that reached the rounding floor and
+        stopped the solve, or -1 when all CG iterations ran (nlinv_cg_stops; waits for the stream)."""
+        nn = int(self.params.newton_steps)
+        out = (C.c_int * nn)()
+        self._check(self._lib.nlinv_cg_stops(self._h, out, nn))
+        return [int(v) for v in out]
 
 
 class NlinvBatch:

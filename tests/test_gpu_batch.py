@@ -77,3 +77,37 @@ def test_batch_rejects_mismatched_frames(data):
         with pytest.raises(ValueError):
             b.reconstruct([torch.zeros((4, 64, 64), dtype=torch.complex64, device="cuda")] * 2,
                           [torch.ones((64, 64), dtype=torch.uint8, device="cuda")] * 2)
+
+
+# Every grid side of the uneven batch workload (128..384, f = n/4 instantiations, fixed 320-thread row lanes) with
+# coil counts up to 16, on a shortened schedule so that the oracle stays within seconds per frame.
+WIDE = [(128, 4, 9), (128, 16, 31), (192, 7, 12), (192, 13, 27), (256, 5, 15), (256, 16, 22), (320, 9, 18),
+        (320, 12, 31), (384, 10, 13), (384, 16, 29)]
+
+
+def test_batch_at_workload_sizes_matches_single_frames_and_oracle():
+    ensure_built()
+    import torch
+    from paper_1301_1215_gb300.nlinv import Nlinv, NlinvBatch
+    NS, NC = 3, 8
+    dev = torch.device("cuda")
+    frames = [noisy_data(n, J, S, 7000 + i) for i, (n, J, S) in enumerate(WIDE)]
+    ys = [_t(torch, y, dev) for _, _, y in frames]
+    ms = [_t(torch, fr.mask, dev) for _, fr, _ in frames]
+    with NlinvBatch([(n, J) for n, J, _ in WIDE], newton_steps=NS, cg_iters=NC) as b:
+        xs, res = b.reconstruct(ys, ms, resid=True)
+        xs = [x.cpu().numpy() for x in xs]
+    seen = set()
+    for i, ((n, J, _), (s, fr, y)) in enumerate(zip(WIDE, frames)):
+        assert np.isfinite(xs[i]).all(), i
+        with Nlinv(n, J, newton_steps=NS, cg_iters=NC) as ctx:
+            xg, rg = ctx.reconstruct(ys[i], ms[i], resid=True)
+        assert rel(xs[i], xg.cpu().numpy()) < 1e-5, (i, n, J)
+        assert np.allclose(res[i], rg, rtol=1e-5), (i, n, J)
+        if n not in seen:           # one frame per grid side against the oracle
+            seen.add(n)
+            y64 = y.astype(np.complex64).astype(np.complex128)
+            xo, ro = O.irgnm(s, fr.mask, y64, synth.initial_guess(n, J), None, NS, NC)
+            assert rel(xs[i], xo) < 1e-3, (i, n, J)
+            assert np.allclose(res[i], ro, rtol=1e-4), (i, n, J)
+    assert seen == {128, 192, 256, 320, 384}

@@ -55,9 +55,14 @@ def test_realtime_frame_384(torch_cuda):
 
 
 def test_precision_frame_512(torch_cuda):
-    """512 x 512 grid, 16 coils, 32 spokes (the precision workload), on a shortened schedule so that the oracle
-    finishes in seconds: the final iterate and every Newton step's residual norm against the oracle."""
-    _compare(torch_cuda, 512, 16, 32, 2, 6, seed=1005)
+    """512 x 512 grid, 16 coils, 32 spokes (the precision workload) on its full schedule, 8 Newton x 30 CG, against
+    the oracle's stored run: every iterate (on the stored sample), every Newton step's residual norm, the final rho
+    on Omega and the final display image."""
+    from tests.helpers import precision_512_errors
+    e = precision_512_errors(torch_cuda, tensor_dft=False)
+    assert max(e["per_step_sample"]) < TOL_X, e
+    assert e["rho_omega"] < TOL_X and e["image"] < TOL_X, e
+    assert max(e["resid_rel"]) < 1e-4, e
 
 
 def test_autotune_picks_a_candidate_and_keeps_parity(torch_cuda):
