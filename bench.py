@@ -189,7 +189,7 @@ def cg_bytes(n: int, J: int, fov: int):
         "row PSF": J * U * 2 * h + mask,
         "col FFT^-1/C^H/FFT": J * U * (h + q + h + q) + q * U,         # T, c in; T, channel products out; rho
         "row W^-H+alpha p": J * U * (h + q) + 2 * J * U + 4 * U,       # T, products, p in; q out; rho: r, p in, p, q out
-        "cg step": 6 * (1 + J) * U,
+        "cg step": 6 * (1 + J) * U,                                    # p, q, r, dx in; dx, r out
     }
 
 
@@ -218,7 +218,8 @@ def run_ours(args, rank, world, local):
                 alpha_q=W.alpha_q, sobolev_a=W.sobolev_a, sobolev_l=W.sobolev_l, use_graph=True, device=dev)
     ys, masks = build_series(torch, ctx, W, frames, dev)
     if args.no_autotune:
-        tuned = {"vec_blocks_per_sm": None, "pdl": None, "candidates": "not run (--no-autotune): compiled defaults"}
+        tuned = {"vec_blocks_per_sm": None, "pdl": None, "split_n1": None, "col_strip": None,
+                 "row_blocks_per_sm": None, "candidates": "not run (--no-autotune): compiled defaults"}
     else:
         tuned = ctx.autotune(ys[0], masks[0], reps=3)   # launch shapes from timed whole-frame graph replays
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
@@ -338,9 +339,12 @@ def run_ours(args, rank, world, local):
                    "n": W.n, "coils": W.ncoils, "spokes": W.spokes, "newton_steps": W.newton_steps,
                    "cg_iters": W.cg_iters, "cg_iterations_executed": cg_exec, "frames_timed": K,
                    "graph": "one CUDA graph per frame",
-                   "launch_shapes": {"vec_blocks_per_sm": tuned["vec_blocks_per_sm"], "pdl": tuned["pdl"],
-                                     "chosen_by": "nlinv_autotune (whole-frame graph replays)",
-                                     "candidates_ms": tuned["candidates"]},
+                   "launch_shapes": {"split_n1": tuned["split_n1"], "col_strip": tuned["col_strip"],
+                                     "row_blocks_per_sm": tuned["row_blocks_per_sm"],
+                                     "vec_blocks_per_sm": tuned["vec_blocks_per_sm"], "pdl": tuned["pdl"],
+                                     "chosen_by": "nlinv_autotune (whole-frame graph replays, one dimension per "
+                                                  "stage: split, column strip, row blocks/SM, vector blocks x PDL)",
+                                     "candidates": tuned["candidates"]},
                    "l2": "flushed before every frame (the frame's ~110 MB working set then stays on chip)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": top, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
@@ -585,7 +589,16 @@ def batch_compare(torch, dev, K=3, Wm=1, profile_only=False):
     torch.cuda.synchronize()
     t_batch = s.elapsed_time(e) / K / 1e3
     launches = batch.launch_count
+    # each batched CG kernel alone (all sides, back to back): its algorithmic bytes over all frames / duration, in
+    # the HBM-bound regime (the frames' ~3.7 GB of workspaces are far larger than L2)
+    bprof = batch.profile_cg(reps=10)
     batch.close()
+    hbm_, _ = peaks()
+    bkern = {}
+    for kname, kms in bprof.items():
+        kb = sum(cg_bytes(n, J, n // 4)[kname] for n, J, _ in shapes)
+        bkern[kname] = {"ms": round(kms, 4), "algo_bytes": int(kb), "gbs": round(kb / (kms * 1e-3) / 1e9, 1),
+                        "frac": round(kb / (kms * 1e-3) / 1e9 / hbm_, 4)}
     ctxs = [Nlinv(n, J, device=dev, **opts) for n, J, _ in shapes]
     xp = [None] * len(ctxs)
     for i, (c, y, m) in enumerate(zip(ctxs, ys, ms)):
@@ -607,6 +620,21 @@ def batch_compare(torch, dev, K=3, Wm=1, profile_only=False):
         if n not in spot:
             d = (xb[i] - xp[i]).abs().pow(2).sum().sqrt() / xp[i].abs().pow(2).sum().sqrt()
             spot[n] = {"frame": i, "coils": J, "rel_l2_batched_vs_plain": float(f"{float(d.item()):.3e}")}
+    # the autotuner on one frame of every grid side (single-frame contexts): does any side want other tile shapes
+    # than the compiled ones the batched kernels use?
+    tuning = {}
+    for i, (n, J, _) in enumerate(shapes):
+        if n in tuning:
+            continue
+        with Nlinv(n, J, device=dev, **opts) as c:
+            t = c.autotune(ys[i], ms[i], reps=3)
+        default = next(cd for cd in t["candidates"] if cd["stage"] == 0)     # stage 0 starts from the defaults
+        tuning[n] = {"coils": J, "chosen": {k: t[k] for k in ("split_n1", "col_strip", "row_blocks_per_sm",
+                                                               "vec_blocks_per_sm", "pdl", "ms_per_frame")},
+                     "compiled_default_ms": default["ms_per_frame"],
+                     "candidates": [[cd["stage"], cd["split_n1"], cd["col_strip"], cd["row_blocks_per_sm"],
+                                     cd["vec_blocks_per_sm"], int(cd["pdl"]), cd["ms_per_frame"]]
+                                    for cd in t["candidates"]]}
     nf = len(shapes)
     total_bytes = sum(frame_bytes(n, J, W.newton_steps, W.cg_iters) for n, J, _ in shapes)
     comp_bytes = sum(compulsory_bytes(n, J) * W.newton_steps * W.cg_iters for n, J, _ in shapes)
@@ -624,7 +652,15 @@ def batch_compare(torch, dev, K=3, Wm=1, profile_only=False):
         "compulsory_gbs": round(comp_bytes / t_batch / 1e9, 1),
         "compulsory_frac": round(comp_bytes / t_batch / 1e9 / hbm, 4), "peak": hbm, "peak_source": src,
         "parity_spot_check": spot, "finite": finite,
-        "l2": "inputs larger than L2 (~0.4 GB working set)",
+        "l2": "inputs larger than L2 (the 64 frames' workspaces hold ~3.7 GB)",
+        "kernels_hbm_bound": {"note": "each batched kernel of one CG iteration launched alone for all sides, 10 times "
+                                      "back to back (nlinv_batch_profile_cg); algorithmic bytes as in "
+                                      "roofline.kernels, summed over the 64 frames; frac of the measured HBM peak",
+                              "kernels": bkern},
+        "autotune_per_side": {"note": "nlinv_autotune on one frame of each side (single-frame context); candidates: "
+                                      "[stage, split_n1, col_strip, row_blocks_per_sm, vec_blocks_per_sm, pdl, "
+                                      "ms_per_frame]; the batched kernels run the compiled split and strip",
+                              "sides": tuning},
     }
 
 

@@ -236,6 +236,14 @@ NLINV_API nlinv_status nlinv_batch_create(const nlinv_params* params, int nframe
  * frame, when the call waited). */
 NLINV_API nlinv_status nlinv_reconstruct_batch(nlinv_batch* batch, int nframes, const nlinv_frame_desc* frames);
 
+/* Times the batched kernels of one CG iteration (the second of the first Newton step) with CUDA events on the
+ * batch's stream, on the workspaces left by the last nlinv_reconstruct_batch (whose CG state it advances; every
+ * frame's solve is first marked running, so that each kernel does its full work): each kernel is launched for all
+ * grid sides, one side after another, reps times back to back between two events.  ms_out (HOST, 6 doubles) gets
+ * the mean duration of one launch set, in the order of nlinv_profile_cg.  Waits for the stream.  Errors: EINVAL
+ * (reps < 1, NULL pointers, no reconstruction yet, fewer than two CG iterations), ECUDA. */
+NLINV_API nlinv_status nlinv_batch_profile_cg(nlinv_batch* batch, int reps, double* ms_out);
+
 /* Kernel launches of one batched reconstruction (the graph's kernel nodes); -1 for NULL. */
 NLINV_API long nlinv_batch_launch_count(const nlinv_batch* batch);
 
@@ -259,26 +267,42 @@ NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
  * Waits for the stream.  Errors: EINVAL (reps < 1, NULL pointers, no reconstruction yet), ECUDA. */
 NLINV_API nlinv_status nlinv_profile_cg(nlinv_ctx* ctx, int reps, double* ms_out);
 
-/* Launch shapes picked by nlinv_autotune. */
+/* Launch shapes picked by nlinv_autotune (one record per timed candidate in its table). */
 typedef struct {
   int vec_blocks_per_sm;  /* blocks per SM of the vector passes (CG step, x update): 2, 4 or 8 */
   int pdl;                /* 1: passes use programmatic dependent launch */
   double ms_per_frame;    /* the measured time of one whole reconstruction with these shapes */
+  int split_n1;           /* N1 of the four-step split n = N1 * N2 of the transforms */
+  int col_strip;          /* adjacent columns per block of the column passes: 4, 8 or 16 */
+  int row_blocks_per_sm;  /* row-pass blocks per SM: 1, 2 or 3 */
+  int stage;              /* table entries: the tuning stage that timed it (0 split, 1 column strip, 2 row blocks,
+                             3 vector blocks x dependent launch) */
 } nlinv_tuning;
 
-/* Autotuner of the launch shapes (not part of the paper's method): reconstructs the caller's representative frame
- * (y, mask, start value x0; DEVICE pointers, as for nlinv_reconstruct) as graph replays for every candidate
- * (vector-pass blocks per SM x dependent launch on/off), reps timed replays each, every one from a cold L2 (a
- * temporary buffer of twice the L2 size is written before it, outside the timing), and keeps the fastest for the
- * context when it beats the compiled default (4 blocks per SM, dependent launch on unless NLINV_PDL=0) by 3 % or
- * more; closer shapes swap places with small changes of conditions, so the default stays.  Whole frames of real data are timed: the passes overlap their neighbours inside a graph, so a pass timed
- * alone can rank shapes wrongly, and an all-zero workspace times differently from data.  The workspace is
- * overwritten.  The choice is cached per (device, n, ncoils, fov, newton_steps, cg_iters) for the process, so a
- * second context of the same shape takes it without timing.  out (HOST) receives the choice and table (HOST,
- * table_len >= 6 entries) every candidate's time, in the order pdl off then on, 2, 4, 8 blocks per SM; either may
- * be NULL.  Errors: EINVAL (NULL or host pointers, reps outside 1..1000, a short table, a batch frame), ECUDA. */
+/* Autotuner of the transforms' tile shapes and the launch shapes (not part of the paper's method): reconstructs the
+ * caller's representative frame (y, mask, start value x0; DEVICE pointers, as for nlinv_reconstruct) as graph
+ * replays, reps timed replays per candidate after one untimed, every one from a cold L2 (a temporary buffer of twice
+ * the L2 size is written before it, outside the timing).  It searches one dimension per stage, each from the best
+ * shapes so far: (0) the four-step split n = N1 * N2 of every transform (the compiled split and, for n = 128 ... 384,
+ * an alternative, e.g. 384 = 12 * 32 beside 16 * 24), (1) the column-strip width of the column passes (4, 8, 16),
+ * (2) the row-pass blocks per SM (1, 2, 3), (3) the vector-pass blocks per SM (2, 4, 8) x dependent launch off/on.
+ * Within a stage a candidate replaces the incumbent only when it is 3 % faster (closer shapes swap places with
+ * small changes of conditions); candidates whose passes do not fit in shared memory are skipped.  The tensor-core
+ * passes (tensor_dft = 1) keep the compiled split and column strips.  Whole frames of real data are timed: the passes
+ * overlap their neighbours inside a graph, so a pass timed alone can rank shapes wrongly, and an all-zero
+ * workspace times differently from data.  The workspace is overwritten.  The choice is cached per (device, n,
+ * ncoils, fov, newton_steps, cg_iters, tensor_dft) for the process, so a second context of the same shape takes it
+ * without timing.  out (HOST) receives the choice and table (HOST, table_len >= 16 entries) every timed candidate in
+ * order (unused entries zeroed); either may be NULL.  Errors: EINVAL (NULL or host pointers, reps outside 1..1000,
+ * a short table, a batch frame), ENOMEM, ECUDA. */
 NLINV_API nlinv_status nlinv_autotune(nlinv_ctx* ctx, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x0,
                                       int reps, nlinv_tuning* out, nlinv_tuning* table, int table_len);
+
+/* Applies the shapes of t (split_n1, col_strip, row_blocks_per_sm, vec_blocks_per_sm, pdl; ms_per_frame and stage
+ * are ignored) to the context, e.g. a choice of nlinv_autotune stored earlier.  Synchronous.  Errors: EINVAL (NULL
+ * t, a split / strip combination not compiled for n, shapes outside the ranges of nlinv_tuning, passes that do not
+ * fit in shared memory, a batch frame, other splits with tensor_dft = 1), ECUDA. */
+NLINV_API nlinv_status nlinv_set_shapes(nlinv_ctx* ctx, const nlinv_tuning* t);
 
 /* Kernel launches queued by the last nlinv_reconstruct, nlinv_forward, ... call (the graph's kernel nodes when a
  * graph was replayed).  -1 for a NULL context. */

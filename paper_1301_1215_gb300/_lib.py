@@ -27,7 +27,12 @@ class Params(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("vec_blocks_per_sm", _int), ("pdl", _int), ("ms_per_frame", _dbl)]
+    """Mirror of nlinv_tuning."""
+    _fields_ = [("vec_blocks_per_sm", _int), ("pdl", _int), ("ms_per_frame", _dbl), ("split_n1", _int),
+                ("col_strip", _int), ("row_blocks_per_sm", _int), ("stage", _int)]
+
+
+TUNE_TABLE = 16   # entries of the nlinv_autotune table
 
 
 class FrameDesc(C.Structure):
@@ -56,6 +61,7 @@ SIGNATURES = {
     "nlinv_batch_create": (_int, [C.POINTER(Params), _int, C.POINTER(FrameDesc), _vp, C.POINTER(_vp)]),
     "nlinv_reconstruct_batch": (_int, [_vp, _int, C.POINTER(FrameDesc)]),
     "nlinv_batch_launch_count": (_long, [_vp]),
+    "nlinv_batch_profile_cg": (_int, [_vp, _int, C.POINTER(_dbl)]),
     "nlinv_batch_destroy": (_int, [_vp]),
     "nlinv_last_launch_count": (_long, [_vp]),
     "nlinv_cg_stops": (_int, [_vp, C.POINTER(_int), _int]),
@@ -63,6 +69,7 @@ SIGNATURES = {
     "nlinv_grid": (_int, [_vp, _int, _vp, _vp, _vp]),
     "nlinv_gridder_destroy": (_int, [_vp]),
     "nlinv_autotune": (_int, [_vp, _vp, _vp, _vp, _int, C.POINTER(Tuning), C.POINTER(Tuning), _int]),
+    "nlinv_set_shapes": (_int, [_vp, C.POINTER(Tuning)]),
     "nlinv_last_error": (C.c_char_p, [_vp]),
 }
 

@@ -103,19 +103,13 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-// True for a launch of the CG iteration whose solve has stopped at its rounding floor (Scalars::flags, latched by
-// the CG step): the block then skips its work -- the stopped solve's remaining iterations are empty steps (the dx
-// they would leave is the one already there).  The flag can be set by block 0 of the CG step while other blocks of
-// that same launch start, so thread 0 reads it once for the whole block.  Every thread of the block must call this
-// (it contains barriers); A.cgskip is the same for the whole block.
+// True for a pass of the CG iteration whose solve has stopped at its rounding floor (Scalars::flags, latched by the
+// CG step): the pass then skips its work -- the stopped solve's remaining iterations are empty steps (the dx they
+// would leave is the one already there).  Only the CG step writes the flag, and every pass starts after the CG step
+// before it has completed (dependent-launch wait), so all threads of a pass read the same value: each reads it
+// itself, with no barrier.  (The CG step takes its own decision block-wide, inside cg_step_body.)
 __device__ __forceinline__ bool cg_stopped(const KArgs& A) {
-  if (!A.cgskip) return false;
-  __shared__ int s_stop;
-  if (threadIdx.x == 0) s_stop = (*(volatile const int*)&A.sc->flags & kFlagCgStopped) != 0;
-  __syncthreads();
-  const bool stop = s_stop != 0;
-  __syncthreads();
-  return stop;
+  return A.cgskip && (*(volatile const int*)&A.sc->flags & kFlagCgStopped) != 0;
 }
 
 // ------------------------------------------------------------------------------------------- geometry ----
@@ -617,9 +611,9 @@ __host__ __device__ inline ColSmem col_smem(int mode, int N, int C, int sm_lane,
   return L;
 }
 
-template <int N1, int N2> struct ColCfg {
+template <int N1, int N2, int CC = NLV_COL_C> struct ColCfg {
   using S = Split<N1, N2>;
-  static constexpr int C = NLV_COL_C;               // adjacent compact columns per block
+  static constexpr int C = CC;                      // adjacent compact columns per block
   static constexpr int THREADS = C * S::TL;
   static_assert(C % 2 == 0, "column staging copies pairs of complex values");
 };
@@ -652,10 +646,10 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
   }
 }
 
-template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc>
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, int CC = NLV_COL_C>
 __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw, TC* tc = nullptr) {
   using S = Split<N1, N2>;
-  constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2>::C;
+  constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2, CC>::C;
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
   const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc;
   const int strips = (Wc + C - 1) / C;
@@ -771,12 +765,12 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
   }
 }
 
-template <int N1, int N2, int MODE, bool STDF = false>
-__global__ void __launch_bounds__(ColCfg<N1, N2>::THREADS) col_pass(const KArgs A) {
+template <int N1, int N2, int MODE, bool STDF = false, int CC = NLV_COL_C>
+__global__ void __launch_bounds__(ColCfg<N1, N2, CC>::THREADS) col_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_enter();
   if (cg_stopped(A)) return;
-  col_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, smem_raw);
+  col_pass_body<N1, N2, MODE, STDF, NoTc, CC>(A, blockIdx.x, smem_raw);
 }
 
 // ------------------------------------------------------------------------------- tensor-core passes ----
@@ -1002,6 +996,52 @@ inline RowGrid row_grid(const SizeKernels* k, int nrows, long rho_pixels, int sm
   g.blocks = (nrows + per - 1) / per;
   g.rho_per_cta = (int)((rho_pixels + g.blocks - 1) / g.blocks);
   return g;
+}
+
+// Tuning variants of a side (nlinv_autotune): the default table with other column-strip widths, and the single-frame
+// passes of an alternative four-step split.  They hold no batch or tensor-core kernels.
+template <int N1, int N2, int CC> SizeKernels make_size_kernels_strip(const SizeKernels& base) {
+  SizeKernels s = base;
+  s.col_lanes = ColCfg<N1, N2, CC>::C;
+  s.col_threads = ColCfg<N1, N2, CC>::THREADS;
+  s.col[COL_IFFT_C] = (const void*)col_pass<N1, N2, COL_IFFT_C, false, CC>;
+  s.col[COL_PROD_FFT] = (const void*)col_pass<N1, N2, COL_PROD_FFT, false, CC>;
+  s.col[COL_SIM_FFT] = (const void*)col_pass<N1, N2, COL_SIM_FFT, false, CC>;
+  s.col[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, false, CC>;
+  s.col[COL_IFFT_ADJ_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_ADJ_FFT, false, CC>;
+  for (int m = 0; m < NUM_COL_MODES; ++m) s.col_std[m] = nullptr;
+  s.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, true, CC>;
+  for (int m = 0; m < NUM_ROW_MODES; ++m) s.row_batch[m] = s.row_std_batch[m] = s.row_tc[m] = s.row_tc_std[m] = nullptr;
+  for (int m = 0; m < NUM_COL_MODES; ++m) s.col_batch[m] = s.col_std_batch[m] = s.col_tc[m] = s.col_tc_std[m] = nullptr;
+  return s;
+}
+
+template <int N1, int N2> SizeKernels make_size_kernels_single() {
+  SizeKernels s{};
+  s.N1 = N1;
+  s.N2 = N2;
+  s.tl = Split<N1, N2>::TL;
+  s.col_lanes = ColCfg<N1, N2>::C;
+  s.col_threads = ColCfg<N1, N2>::THREADS;
+  s.sm_lane = Split<N1, N2>::SM_LANE;
+  s.sm_lane_col = Split<N1, N2>::SM_LANE_COL;
+  s.row[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT>;
+  s.row[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF>;
+  s.row[ROW_FFT_P_OUT] = (const void*)row_pass<N1, N2, ROW_FFT_P_OUT>;
+  s.row[ROW_FFT_RESID] = (const void*)row_pass<N1, N2, ROW_FFT_RESID>;
+  s.row[ROW_P_IFFT] = (const void*)row_pass<N1, N2, ROW_P_IFFT>;
+  s.row[ROW_FFT_W_ADJ] = (const void*)row_pass<N1, N2, ROW_FFT_W_ADJ>;
+  s.row[ROW_FFT_W_NORMAL] = (const void*)row_pass<N1, N2, ROW_FFT_W_NORMAL>;
+  s.row[ROW_FFT_W_RHS] = (const void*)row_pass<N1, N2, ROW_FFT_W_RHS>;
+  s.col[COL_IFFT_C] = (const void*)col_pass<N1, N2, COL_IFFT_C>;
+  s.col[COL_PROD_FFT] = (const void*)col_pass<N1, N2, COL_PROD_FFT>;
+  s.col[COL_SIM_FFT] = (const void*)col_pass<N1, N2, COL_SIM_FFT>;
+  s.col[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT>;
+  s.col[COL_IFFT_ADJ_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_ADJ_FFT>;
+  s.row_std[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF, true>;
+  s.row_std[ROW_FFT_W_NORMAL] = (const void*)row_pass<N1, N2, ROW_FFT_W_NORMAL, true>;
+  s.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, true>;
+  return s;
 }
 
 template <int N1, int N2> SizeKernels make_size_kernels() {

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -65,6 +66,7 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
   if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
   if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
   __shared__ float s_alpha;
+  __shared__ int s_skip;
   __shared__ double red[32];
   double t = 0.0;
   for (int k = threadIdx.x; k < A.n_pq; k += blockDim.x) t += A.pq_part[k];
@@ -95,8 +97,10 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
       }
     }
     s_alpha = (float)a;
+    s_skip = was_stopped ? 1 : 0;     // stopped by an earlier iteration: nothing to update
   }
   __syncthreads();
+  if (s_skip) return;                 // the same for the whole block (thread 0 decided for it)
   const float a = s_alpha;
   double accd = 0.0;
   while (i < A.n2) {
@@ -150,7 +154,6 @@ __global__ void image_kernel(const KArgs A) {
 
 __global__ void cg_step_kernel(const KArgs A) {
   nlv::pdl_enter();
-  if (nlv::cg_stopped(A)) return;
   cg_step_body(A, blockIdx.x, gridDim.x);
 }
 __global__ void add_kernel(const KArgs A) {
@@ -193,7 +196,6 @@ __global__ void cg_step_batch(const nlv::BatchArgs B) {
   for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
     int bid, nblk;
     const KArgs& A = nlv::batch_frame(B, w, bid, nblk);
-    if (nlv::cg_stopped(A)) continue;
     cg_step_body(A, bid, nblk);
   }
 }
@@ -208,7 +210,7 @@ __global__ void add_batch(const nlv::BatchArgs B) {
 
 constexpr int kVecThreads = 256;
 constexpr int kTuneVecMax = 8;       // largest vector-kernel blocks per SM that nlinv_autotune tries
-constexpr int kTuneCandidates = 6;   // its candidates: {2, 4, 8} blocks per SM x dependent launch off / on
+constexpr int kTuneMaxCandidates = 16;   // most candidates it times (2 splits + 3 strips + 3 row + 6 vector shapes)
 constexpr double kTuneMargin = 0.03; // a candidate replaces the compiled default only when this much faster
 #ifndef NLV_VEC_BLOCKS_PER_SM
 #define NLV_VEC_BLOCKS_PER_SM 4   // blocks per SM of the vector passes
@@ -692,6 +694,66 @@ nlinv_status nlinv_default_params(nlinv_params* p, int n, int ncoils) {
 
 namespace {
 
+// Twiddle tables of the context's split: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise
+// for (N2, N1).  Synchronous.
+cudaError_t upload_twiddles(nlinv_ctx* c) {
+  const int N = c->N, N1 = c->k->N1, N2 = c->k->N2;
+  std::vector<float2> ta(N), tb(N);
+  auto tw = [N](long m) {
+    m %= N;
+    const double t = 2.0 * 3.14159265358979323846 * (double)m / (double)N;
+    return make_float2((float)std::cos(t), (float)-std::sin(t));
+  };
+  for (int k2 = 0; k2 < N2; ++k2)
+    for (int a = 0; a < N1; ++a) ta[k2 * N1 + a] = tw((long)a * k2);
+  for (int k2 = 0; k2 < N1; ++k2)
+    for (int a = 0; a < N2; ++a) tb[k2 * N2 + a] = tw((long)a * k2);
+  cudaError_t e = cudaMemcpy(c->twA, ta.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->twB, tb.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Raises the dynamic shared-memory limit of every single-frame pass of table k for the context's shapes; false
+// when one of them needs more than the device allows.
+bool allow_passes(nlinv_ctx* c, const SizeKernels* k) {
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  const SizeKernels* saved = c->k;
+  c->k = k;
+  const int lanes = std::max(row_geom(c, false).lanes, row_geom(c, true).lanes);
+  c->k = saved;
+  auto allow = [&](const void* fn, size_t need) {
+    if (!fn) return true;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) { cudaGetLastError(); return false; }
+    const int dyn_max = smem_optin - (int)fa.sharedSizeBytes;
+    if ((size_t)dyn_max < need) return false;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  bool ok = true;
+  for (int m = 0; m < nlv::NUM_ROW_MODES && ok; ++m)
+    ok = allow(k->row[m], k->row_smem(m, lanes)) && allow(k->row_std[m], k->row_smem(m, lanes));
+  for (int m = 0; m < nlv::NUM_COL_MODES && ok; ++m)
+    ok = allow(k->col[m], k->col_smem(m, c->Wc)) && allow(k->col_std[m], k->col_smem(m, c->Wc));
+  return ok;
+}
+
+// Switches the context to the kernel table k (a tuning variant of its side): false, and no change, when its passes
+// do not fit; rewrites the twiddle tables when the split differs.  Drops the captured graph.
+bool use_variant(nlinv_ctx* c, const SizeKernels* k) {
+  if (k == c->k) return true;
+  if (!allow_passes(c, k)) return false;
+  const bool resplit = k->N1 != c->k->N1;
+  c->k = k;
+  if (resplit && upload_twiddles(c) != cudaSuccess) return false;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return true;
+}
+
 // Context set-up shared by nlinv_create and the frames of a batch (batch_lanes > 0: fixed row-pass block shape).
 nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lanes, nlinv_ctx** out) {
   nlinv_ctx* c = nullptr;
@@ -826,18 +888,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
   c->sc = (Scalars*)take(scb);
   if (c->tc) c->tcB = take(tcb);
 
-  // twiddle tables: twA[k2*N1 + a] = exp(-2 pi i a k2 / N) (a < N1, k2 < N2), twB likewise for (N2, N1)
-  const int N = c->N, N1 = c->k->N1, N2 = c->k->N2;
-  std::vector<float2> ta(N), tb(N);
-  auto tw = [N](long m) {
-    m %= N;
-    const double t = 2.0 * 3.14159265358979323846 * (double)m / (double)N;
-    return make_float2((float)std::cos(t), (float)-std::sin(t));
-  };
-  for (int k2 = 0; k2 < N2; ++k2)
-    for (int a = 0; a < N1; ++a) ta[k2 * N1 + a] = tw((long)a * k2);
-  for (int k2 = 0; k2 < N1; ++k2)
-    for (int a = 0; a < N2; ++a) tb[k2 * N2 + a] = tw((long)a * k2);
+  const int N = c->N;
   // Sobolev weight w(k) = (1 + a |k|^2)^(-l/2), |k|^2 = (g1^2 + g2^2) / N^2 with signed natural-order indices
   std::vector<float> wt((size_t)c->plane);
   for (int k1 = 0; k1 < N; ++k1)
@@ -847,8 +898,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
       wt[(size_t)k1 * N + k2] = (float)std::pow(1.0 + params->sobolev_a * kk, -0.5 * params->sobolev_l);
     }
   e = cudaMemset(c->base, 0, total);
-  if (e == cudaSuccess) e = cudaMemcpy(c->twA, ta.data(), N * cplx, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->twB, tb.data(), N * cplx, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload_twiddles(c);
   if (e == cudaSuccess) e = cudaMemcpy(c->wtab, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && c->tc) {
     std::vector<uint16_t> bt(nlv::kTcBBytes / 2);
@@ -1265,6 +1315,32 @@ nlinv_status nlinv_cg_stops(nlinv_ctx* c, int* out, int len) {
   return NLINV_OK;
 }
 
+nlinv_status nlinv_set_shapes(nlinv_ctx* c, const nlinv_tuning* t) {
+  if (!c) return NLINV_EINVAL;
+  if (!t) return fail(c, NLINV_EINVAL, "t is NULL");
+  if (c->batch_lanes > 0) return fail(c, NLINV_EINVAL, "batch frames keep the batch's shapes");
+  if (t->vec_blocks_per_sm < 1 || t->vec_blocks_per_sm > kTuneVecMax)
+    return fail(c, NLINV_EINVAL, "vec_blocks_per_sm must be in 1..8");
+  if (t->row_blocks_per_sm < 1 || t->row_blocks_per_sm > 3) return fail(c, NLINV_EINVAL, "row_blocks_per_sm must be in 1..3");
+  const SizeKernels* variants[8];
+  const int nvar = nlv::size_variants(c->N, variants, 8);
+  const SizeKernels* pick = nullptr;
+  for (int v = 0; v < nvar && !pick; ++v)
+    if (variants[v]->N1 == t->split_n1 && variants[v]->col_lanes == t->col_strip) pick = variants[v];
+  if (!pick) return fail(c, NLINV_EINVAL, "no compiled transform with that split and column strip for this n");
+  if (c->tc && pick != variants[0]) return fail(c, NLINV_EINVAL, "the tensor-core passes keep the compiled split and strips");
+  const int saved_rc = c->row_ctas_per_sm;
+  c->row_ctas_per_sm = t->row_blocks_per_sm;
+  if (!use_variant(c, pick) || !allow_passes(c, c->k)) {
+    c->row_ctas_per_sm = saved_rc;
+    return fail(c, NLINV_EINVAL, "the passes of these shapes do not fit in shared memory");
+  }
+  c->vec_blocks = c->sms * t->vec_blocks_per_sm;
+  c->pdl = t->pdl != 0;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return NLINV_OK;
+}
+
 nlinv_status nlinv_autotune(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mask, const nlinv_c32* x0, int reps,
                             nlinv_tuning* out, nlinv_tuning* table, int table_len) {
   if (!c) return NLINV_EINVAL;
@@ -1272,39 +1348,54 @@ nlinv_status nlinv_autotune(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mas
   if ((st = check_dev(c, y, "y")) || (st = check_dev(c, mask, "mask")) || (st = check_dev(c, x0, "x0"))) return st;
   if (reps < 1 || reps > 1000) return fail(c, NLINV_EINVAL, "reps must be in 1..1000");
   if (c->batch_lanes > 0) return fail(c, NLINV_EINVAL, "batch frames are not tuned one by one");
-  if (table && table_len < kTuneCandidates) return fail(c, NLINV_EINVAL, "table needs 6 entries");
-  struct Key { int dev, n, J, fov, newton, cg; };
-  struct Entry { Key k; nlinv_tuning t; nlinv_tuning all[kTuneCandidates]; };
+  if (table && table_len < kTuneMaxCandidates)
+    return fail(c, NLINV_EINVAL, "table needs " + std::to_string(kTuneMaxCandidates) + " entries");
+  struct Key { int dev, n, J, fov, newton, cg, tc; };
+  struct Entry { Key k; const SizeKernels* kern; nlinv_tuning t; std::vector<nlinv_tuning> all; };
   static std::mutex mtx;
   static std::vector<Entry> cache;
-  const Key key{c->device, c->N, c->J, c->f, c->prm.newton_steps, c->prm.cg_iters};
+  const Key key{c->device, c->N, c->J, c->f, c->prm.newton_steps, c->prm.cg_iters, c->tc ? 1 : 0};
   auto same = [&](const Key& a) {
     return a.dev == key.dev && a.n == key.n && a.J == key.J && a.fov == key.fov && a.newton == key.newton &&
-           a.cg == key.cg;
+           a.cg == key.cg && a.tc == key.tc;
   };
-  auto apply = [&](const nlinv_tuning& t) {
-    c->vec_blocks = c->sms * t.vec_blocks_per_sm;
-    c->pdl = t.pdl != 0;
+  // the context's launch shapes as one tuning record (ms_per_frame and stage filled by the caller)
+  auto shape = [&]() {
+    nlinv_tuning t{};
+    t.vec_blocks_per_sm = c->vec_blocks / c->sms;
+    t.pdl = c->pdl ? 1 : 0;
+    t.split_n1 = c->k->N1;
+    t.col_strip = c->k->col_lanes;
+    t.row_blocks_per_sm = c->row_ctas_per_sm;
+    return t;
+  };
+  auto set_shapes = [&](int vbk, bool pdl, int row_ctas) {
+    c->vec_blocks = c->sms * vbk;
+    c->pdl = pdl;
+    c->row_ctas_per_sm = row_ctas;
     if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   };
   {
     std::lock_guard<std::mutex> lk(mtx);
     for (const Entry& e : cache)
       if (same(e.k)) {
-        apply(e.t);
+        if (!use_variant(c, e.kern)) return fail(c, NLINV_ECUDA, "nlinv_autotune: cached variant does not fit");
+        set_shapes(e.t.vec_blocks_per_sm, e.t.pdl != 0, e.t.row_blocks_per_sm);
         if (out) *out = e.t;
-        if (table) std::copy(e.all, e.all + kTuneCandidates, table);
+        if (table) {
+          for (int i = 0; i < table_len; ++i) table[i] = nlinv_tuning{};
+          std::copy(e.all.begin(), e.all.end(), table);
+        }
         return NLINV_OK;
       }
   }
-  // Whole reconstructions of the caller's frame, replayed as graphs (each replay starts from the last result, as
-  // in a series): only the whole graph shows how neighbouring passes overlap, and an all-zero workspace times
-  // differently from data.
+  // Whole reconstructions of the caller's frame, replayed as graphs (each replay starts from the same start value):
+  // only the whole graph shows how neighbouring passes overlap, and an all-zero workspace times differently from
+  // data.  Every timed replay starts with a cold L2 (a write of twice its size outside the events), as a frame of a
+  // series does after the rest of an application has run.
   const size_t vb = c->vec * sizeof(float2), db = (size_t)c->J * c->plane * sizeof(float2);
   NLV_TRY(cudaMemcpyAsync(c->y, y, db, cudaMemcpyDeviceToDevice, c->stream), "copy y");
   NLV_TRY(cudaMemcpyAsync(c->mask, mask, (size_t)c->plane, cudaMemcpyDeviceToDevice, c->stream), "copy mask");
-  // every timed replay starts with a cold L2 (a write of twice its size outside the events), as a frame of a
-  // series does after the rest of an application has run
   int l2 = 0;
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
   const size_t flush_bytes = std::max<size_t>(2 * (size_t)l2, 64u << 20);
@@ -1318,65 +1409,121 @@ nlinv_status nlinv_autotune(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* mas
     cudaError_t ee = cudaEventCreate(&ev[i]);
     if (ee != cudaSuccess) { cudaFree(flush); return cuda_fail(c, ee, "event create"); }
   }
-  const int vbs[] = {2, 4, kTuneVecMax};
-  nlinv_tuning best{};
-  best.ms_per_frame = 1e30;
-  nlinv_tuning dflt{NLV_VEC_BLOCKS_PER_SM, c->pdl ? 1 : 0, 0.0};   // the compiled default (and the PDL setting)
-  Entry ent{};
-  int ncand = 0;
   cudaError_t e = cudaSuccess;
-  for (int pdl = 0; pdl < 2 && e == cudaSuccess; ++pdl)
-    for (int vbk : vbs) {
-      if (e != cudaSuccess) break;
-      nlinv_tuning t{vbk, pdl, 0.0};
-      apply(t);
+  // ms per frame of the context's current shapes
+  auto time_frame = [&]() -> double {
+    if (e != cudaSuccess) return 1e30;
+    e = cudaMemcpyAsync(c->x, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->xref, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return 1e30;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return 1e30;
+    cudaError_t e1 = q_reconstruct(c);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    e = e1 != cudaSuccess ? e1 : e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    double tot = 0.0;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {          // r = 0: warm-up
       e = cudaMemcpyAsync(c->x, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(c->xref, x0, vb, cudaMemcpyDeviceToDevice, c->stream);
-      if (e != cudaSuccess) break;
-      cudaGraph_t g = nullptr;
-      cudaGraphExec_t ge = nullptr;
-      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) break;
-      cudaError_t e1 = q_reconstruct(c);
-      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-      e = e1 != cudaSuccess ? e1 : e2;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
-      if (g) cudaGraphDestroy(g);
-      if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);                 // warm-up
-      double tot = 0.0;
-      for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        e = cudaMemsetAsync(flush, r & 0xff, flush_bytes, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
-        if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        tot += ms;
-      }
-      if (ge) cudaGraphExecDestroy(ge);
-      t.ms_per_frame = tot / reps;
-      if (e == cudaSuccess) ent.all[ncand++] = t;
-      if (e == cudaSuccess && t.ms_per_frame < best.ms_per_frame) best = t;
-      if (e == cudaSuccess && t.vec_blocks_per_sm == dflt.vec_blocks_per_sm && t.pdl == dflt.pdl) dflt = t;
+      if (e == cudaSuccess) e = cudaMemsetAsync(flush, r & 0xff, flush_bytes, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+      if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (r > 0) tot += ms;
     }
+    if (ge) cudaGraphExecDestroy(ge);
+    return e == cudaSuccess ? tot / reps : 1e30;
+  };
+  Entry ent{};
+  // Coordinate descent, one launch-shape dimension per stage, each from the best shapes of the stages before:
+  // stage 0 the four-step split of the transforms, 1 the column-strip width, 2 the row-pass blocks per SM, 3 the
+  // vector-pass blocks per SM with dependent launch off and on.  Within a stage a candidate replaces the incumbent
+  // only when it is kTuneMargin faster (closer shapes swap places with small changes of conditions).
+  const SizeKernels* variants[8];
+  const int nvar = nlv::size_variants(c->N, variants, 8);
+  const SizeKernels* base = c->k;
+  auto stage = [&](int id, const std::vector<std::function<bool()>>& cands) {
+    // cands[0] restores the incumbent; each candidate applies its shapes and returns false if they do not fit
+    double inc_ms = -1.0;
+    int best = 0;
+    double best_ms = 1e30;
+    for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+      if (!cands[i]()) continue;
+      nlinv_tuning t = shape();
+      t.ms_per_frame = time_frame();
+      t.stage = id;
+      if (e != cudaSuccess) break;
+      ent.all.push_back(t);
+      if (i == 0) inc_ms = t.ms_per_frame;
+      if (t.ms_per_frame < best_ms) { best_ms = t.ms_per_frame; best = (int)i; }
+    }
+    if (inc_ms > 0.0 && best_ms > (1.0 - kTuneMargin) * inc_ms) best = 0;
+    if (e == cudaSuccess) cands[best]();
+  };
+  // stage 0: splits (the default table, and the alternative split if the side has one; the tensor-core passes
+  // exist for the default split only)
+  {
+    std::vector<std::function<bool()>> cands{[&] { return use_variant(c, base); }};
+    for (int v = 1; v < nvar && !c->tc; ++v)
+      if (variants[v]->N1 != base->N1) cands.push_back([&, v] { return use_variant(c, variants[v]); });
+    stage(0, cands);
+  }
+  // stage 1: column strips of the chosen split (variants of the default split only)
+  if (c->k->N1 == base->N1 && !c->tc) {
+    std::vector<std::function<bool()>> cands{[&] { return use_variant(c, base); }};
+    for (int v = 1; v < nvar; ++v)
+      if (variants[v]->N1 == base->N1 && variants[v]->col_lanes != base->col_lanes)
+        cands.push_back([&, v] { return use_variant(c, variants[v]); });
+    stage(1, cands);
+  }
+  // stage 2: row-pass blocks per SM
+  {
+    const int inc = c->row_ctas_per_sm;
+    std::vector<std::function<bool()>> cands{[&, inc] { set_shapes(c->vec_blocks / c->sms, c->pdl, inc); return true; }};
+    for (int rc : {1, 2, 3})
+      if (rc != inc)
+        cands.push_back([&, rc] { set_shapes(c->vec_blocks / c->sms, c->pdl, rc); return allow_passes(c, c->k); });
+    stage(2, cands);
+  }
+  // stage 3: vector-pass blocks per SM x dependent launch
+  {
+    const int ivb = c->vec_blocks / c->sms;
+    const bool ipdl = c->pdl;
+    std::vector<std::function<bool()>> cands{[&, ivb, ipdl] { set_shapes(ivb, ipdl, c->row_ctas_per_sm); return true; }};
+    for (int pdl = 0; pdl < 2; ++pdl)
+      for (int vbk : {2, 4, kTuneVecMax})
+        if (vbk != ivb || (pdl != 0) != ipdl)
+          cands.push_back([&, vbk, pdl] { set_shapes(vbk, pdl != 0, c->row_ctas_per_sm); return true; });
+    stage(3, cands);
+  }
   for (int i = 0; i < 2; ++i) cudaEventDestroy(ev[i]);
   cudaFree(flush);
   int zero = 0;   // the timing runs are not the caller's results: drop any flag they raised
   if (e == cudaSuccess) e = cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "nlinv_autotune");
-  // Shapes within a few per cent swap places with small changes of conditions (other work between frames, the
-  // frame's own copies); the default stays unless a candidate beats it clearly.
-  if (dflt.ms_per_frame > 0.0 && best.ms_per_frame > (1.0 - kTuneMargin) * dflt.ms_per_frame) best = dflt;
-  apply(best);
   ent.k = key;
-  ent.t = best;
+  ent.kern = c->k;
+  ent.t = shape();
+  // the chosen shapes' own measurement: the last stage's entry for them
+  for (const nlinv_tuning& t : ent.all)
+    if (t.vec_blocks_per_sm == ent.t.vec_blocks_per_sm && t.pdl == ent.t.pdl && t.split_n1 == ent.t.split_n1 &&
+        t.col_strip == ent.t.col_strip && t.row_blocks_per_sm == ent.t.row_blocks_per_sm)
+      ent.t.ms_per_frame = t.ms_per_frame, ent.t.stage = t.stage;
   {
     std::lock_guard<std::mutex> lk(mtx);
     cache.push_back(ent);
   }
-  if (out) *out = best;
-  if (table) std::copy(ent.all, ent.all + kTuneCandidates, table);
+  if (out) *out = ent.t;
+  if (table) {
+    for (int i = 0; i < table_len; ++i) table[i] = nlinv_tuning{};
+    std::copy(ent.all.begin(), ent.all.end(), table);
+  }
   return NLINV_OK;
 }
 
@@ -1402,6 +1549,8 @@ struct nlinv_batch {
   };
   std::vector<Launch> launches;
   cudaGraphExec_t graph = nullptr;
+  bool have_state = false;                  // a reconstruction has filled the workspaces
+  std::vector<size_t> group_first;          // index in `launches` of each group's first launch
   bool pdl = true;
   bool multi = false;                       // one launch per pass for all sides the multi-side kernels cover
                                             // (NLINV_BATCH_MULTI=1; measured slower, see nlinv_batch_create)
@@ -1455,6 +1604,22 @@ const void* batched_kernel(const SizeKernels* k, const void* fn) {
   if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
   if (fn == (const void*)add_kernel) return (const void*)add_batch;
   return nullptr;
+}
+
+// One batched launch on stream st (with the batch's dependent-launch setting).
+cudaError_t launch_batched(nlinv_batch* b, nlinv_batch::Launch& bl, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(bl.grid);
+  cfg.blockDim = dim3(bl.block);
+  cfg.dynamicSmemBytes = bl.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = b->pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {&bl.args};
+  return cudaLaunchKernelExC(&cfg, bl.fn, args);
 }
 
 nlinv_status batch_fail(nlinv_batch* b, nlinv_status st, const std::string& msg) {
@@ -1533,6 +1698,7 @@ nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const n
     for (int i : fr)
       if (recs[i].size() != L) return batch_fail(b, NLINV_EINVAL, "frames of one grid side differ in schedule");
     const bool multi = sides[g] == 0;
+    b->group_first.push_back(b->launches.size());
     for (size_t l = 0; l < L; ++l) {
       nlinv_batch::Launch bl{};
       bl.group = (int)g;
@@ -1608,21 +1774,8 @@ nlinv_status nlinv_batch_create(const nlinv_params* params, int nframes, const n
   e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, b->stream);
   for (size_t g = 1; g < G && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(b->gstream[g], b->ev_fork, 0);
-  for (size_t l = 0; l < b->launches.size() && e == cudaSuccess; ++l) {
-    nlinv_batch::Launch& bl = b->launches[l];
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(bl.grid);
-    cfg.blockDim = dim3(bl.block);
-    cfg.dynamicSmemBytes = bl.smem;
-    cfg.stream = b->gstream[bl.group];
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = b->pdl ? 1 : 0;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    void* args[] = {&bl.args};
-    e = cudaLaunchKernelExC(&cfg, bl.fn, args);
-  }
+  for (size_t l = 0; l < b->launches.size() && e == cudaSuccess; ++l)
+    e = launch_batched(b, b->launches[l], b->gstream[b->launches[l].group]);
   for (size_t g = 1; g < G && e == cudaSuccess; ++g) {
     e = cudaEventRecord(b->ev_join[g], b->gstream[g]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join[g], 0);
@@ -1663,6 +1816,7 @@ nlinv_status nlinv_reconstruct_batch(nlinv_batch* b, int nframes, const nlinv_fr
       e = cudaMemcpyAsync(c->xref, d.x_ref ? (const void*)d.x_ref : (const void*)c->x, vb, cudaMemcpyDefault, b->stream);
   }
   if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, b->stream);
+  if (e == cudaSuccess) b->have_state = true;
   for (int i = 0; i < nframes && e == cudaSuccess; ++i) {
     nlinv_ctx* c = b->frames[i];
     e = cudaMemcpyAsync(frames[i].x_inout, c->x, c->vec * sizeof(float2), cudaMemcpyDefault, b->stream);
@@ -1689,6 +1843,52 @@ nlinv_status nlinv_reconstruct_batch(nlinv_batch* b, int nframes, const nlinv_fr
 }
 
 long nlinv_batch_launch_count(const nlinv_batch* b) { return b ? (long)b->launches.size() : -1; }
+
+nlinv_status nlinv_batch_profile_cg(nlinv_batch* b, int reps, double* ms_out) {
+  if (!b) return NLINV_EINVAL;
+  if (reps < 1 || !ms_out) return fail(nullptr, NLINV_EINVAL, "reps must be >= 1 and ms_out non-NULL");
+  if (!b->have_state) return fail(nullptr, NLINV_EINVAL, "run nlinv_reconstruct_batch before nlinv_batch_profile_cg");
+  if (b->prm.cg_iters < 2) return fail(nullptr, NLINV_EINVAL, "the batch's schedule has fewer than two CG iterations");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  // every frame's solve is marked running, so that every kernel does its full work
+  for (nlinv_ctx* c : b->frames) {
+    int flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flags, &c->sc->flags, sizeof(int), cudaMemcpyDeviceToHost);
+    flags &= ~nlv::kFlagCgStopped;
+    if (e == cudaSuccess) e = cudaMemcpy(&c->sc->flags, &flags, sizeof(int), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return fail(nullptr, NLINV_ECUDA, std::string("nlinv_batch_profile_cg: ") + cudaGetErrorString(e));
+  // the six launches of the second CG iteration of the first Newton step, in every group: they end at the group's
+  // second CG step
+  std::vector<size_t> first6;
+  for (size_t g = 0; g < b->group_first.size(); ++g) {
+    const size_t end = g + 1 < b->group_first.size() ? b->group_first[g + 1] : b->launches.size();
+    int seen = 0;
+    size_t at = 0;
+    for (size_t l = b->group_first[g]; l < end && seen < 2; ++l)
+      if (b->launches[l].fn == (const void*)cg_step_batch && ++seen == 2) at = l;
+    if (seen < 2 || at < b->group_first[g] + 5) return fail(nullptr, NLINV_EINVAL, "internal: CG launches not found");
+    first6.push_back(at - 5);
+  }
+  cudaEvent_t ev[2];
+  for (int i = 0; i < 2; ++i)
+    if ((e = cudaEventCreate(&ev[i])) != cudaSuccess)
+      return fail(nullptr, NLINV_ECUDA, std::string("event create: ") + cudaGetErrorString(e));
+  for (int k = 0; k < kProfileKernels && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(ev[0], b->stream);
+    for (int it = 0; it < reps && e == cudaSuccess; ++it)
+      for (size_t g = 0; g < first6.size() && e == cudaSuccess; ++g)
+        e = launch_batched(b, b->launches[first6[g] + k], b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], b->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    ms_out[k] = ms / reps;
+  }
+  for (int i = 0; i < 2; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return fail(nullptr, NLINV_ECUDA, std::string("nlinv_batch_profile_cg: ") + cudaGetErrorString(e));
+  return NLINV_OK;
+}
 
 nlinv_status nlinv_batch_destroy(nlinv_batch* b) {
   batch_free(b);

@@ -13,6 +13,18 @@ const SizeKernels* sizes_256(int n);
 const SizeKernels* sizes_384(int n);
 const SizeKernels* sizes_512(int n);
 
+// Tuning variants of side n (defined in sizes_tune_*.cu): up to max tables (the default first, then column strips
+// of 4 and 16, then an alternative four-step split); returns their number (1 when n has no variants).
+int size_variants_a(int n, const SizeKernels** out, int max);
+int size_variants_b(int n, const SizeKernels** out, int max);
+const SizeKernels* find_size(int n);
+inline int size_variants(int n, const SizeKernels** out, int max) {
+  int k = size_variants_a(n, out, max);
+  if (k == 0) k = size_variants_b(n, out, max);
+  if (k == 0 && max > 0 && find_size(n)) { out[0] = find_size(n); k = 1; }
+  return k;
+}
+
 inline const SizeKernels* find_size(int n) {
   const SizeKernels* s = nullptr;
   if (!s) s = sizes_small(n);

@@ -257,25 +257,36 @@ class Nlinv:
 
     def autotune(self, y: torch.Tensor, mask: torch.Tensor, x0: Optional[torch.Tensor] = None,
                  reps: int = 3) -> dict:
-        """Picks the launch shapes by timing whole graph-replayed reconstructions of a representative frame
-        (nlinv_autotune; x0 default: rho = 1, chat = 0); overwrites the workspace.  Returns the choice
-        (vector-pass blocks per SM, dependent launch on/off, ms per frame; the compiled default unless a candidate
-        is 3 % faster) and every candidate's time."""
+        """Picks the transforms' split and column strips and the launch shapes by timing whole graph-replayed
+        reconstructions of a representative frame (nlinv_autotune; x0 default: rho = 1, chat = 0), one dimension
+        per stage; overwrites the workspace.  Returns the choice and every timed candidate (a dict each)."""
         y, mask = self._y(y), self._m(mask)
         if x0 is None:
             x0 = torch.zeros(self._shape_x(), dtype=torch.complex64, device=self.device)
             x0[0] = 1.0
         x0 = self._x(x0, "x0")
         t = _lib.Tuning()
-        table = (_lib.Tuning * 6)()
+        table = (_lib.Tuning * _lib.TUNE_TABLE)()
         self._begin()
         self._check(self._lib.nlinv_autotune(self._h, _ptr(y), _ptr(mask), _ptr(x0), int(reps), C.byref(t),
-                                             table, 6))
+                                             table, _lib.TUNE_TABLE))
         self._end()
-        return {"vec_blocks_per_sm": int(t.vec_blocks_per_sm), "pdl": bool(t.pdl),
-                "ms_per_frame": float(t.ms_per_frame),
-                "candidates": [(int(e.vec_blocks_per_sm), bool(e.pdl), round(float(e.ms_per_frame), 4))
-                               for e in table]}
+
+        def rec(e):
+            return {"split_n1": int(e.split_n1), "col_strip": int(e.col_strip),
+                    "row_blocks_per_sm": int(e.row_blocks_per_sm), "vec_blocks_per_sm": int(e.vec_blocks_per_sm),
+                    "pdl": bool(e.pdl), "ms_per_frame": round(float(e.ms_per_frame), 4), "stage": int(e.stage)}
+        out = rec(t)
+        out["candidates"] = [rec(e) for e in table if e.ms_per_frame > 0]
+        return out
+
+    def set_shapes(self, split_n1: int, col_strip: int = 8, row_blocks_per_sm: int = 2, vec_blocks_per_sm: int = 4,
+                   pdl: bool = True) -> None:
+        """Applies explicit tile and launch shapes (nlinv_set_shapes), e.g. a stored nlinv_autotune choice."""
+        t = _lib.Tuning()
+        t.split_n1, t.col_strip, t.row_blocks_per_sm = int(split_n1), int(col_strip), int(row_blocks_per_sm)
+        t.vec_blocks_per_sm, t.pdl = int(vec_blocks_per_sm), 1 if pdl else 0
+        self._check(self._lib.nlinv_set_shapes(self._h, C.byref(t)))
 
     @property
     def last_launch_count(self) -> int:
@@ -343,6 +354,13 @@ class NlinvBatch:
     @property
     def launch_count(self) -> int:
         return int(self._lib.nlinv_batch_launch_count(self._h))
+
+    def profile_cg(self, reps: int = 10) -> dict:
+        """CUDA-event duration (ms) of each batched kernel of one CG iteration, all grid sides, launched ``reps``
+        times back to back on the state of the last batched reconstruction (nlinv_batch_profile_cg)."""
+        ms = (C.c_double * len(Nlinv.CG_KERNELS))()
+        _lib.check(self._lib.nlinv_batch_profile_cg(self._h, int(reps), ms), None)
+        return dict(zip(Nlinv.CG_KERNELS, [float(v) for v in ms]))
 
     def reconstruct(self, ys, masks, xs=None, x_refs=None, resid: bool = False):
         """Reconstructs every frame.  ``xs`` (start values, overwritten with the results; default rho = 1,

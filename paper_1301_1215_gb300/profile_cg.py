@@ -3,7 +3,8 @@
 
     ncu --set full --clock-control none --nvtx --nvtx-include "cgprof/" -o prof python -m paper_1301_1215_gb300.profile_cg
 
-Defaults: the real-time workload (384 x 384 grid, 10 coils, 13 spokes, 7 Newton steps x 30 CG iterations).
+Defaults: the real-time workload (384 x 384 grid, 10 coils, 13 spokes, 7 Newton steps x 30 CG iterations);
+--tensor-dft runs the passes with their radix-16 stages on the tensor cores (n = 256, 512).
 """
 from __future__ import annotations
 
@@ -23,10 +24,11 @@ def main(argv=None) -> None:
     ap.add_argument("--coils", type=int, default=10)
     ap.add_argument("--spokes", type=int, default=13)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--tensor-dft", action="store_true", help="radix-16 DFT stages on the tensor cores")
     args = ap.parse_args(argv)
     fr = synth.make_frame(args.n, args.coils, args.spokes, seed=1003)
     dev = torch.device("cuda")
-    with Nlinv(args.n, args.coils, use_graph=False) as ctx:
+    with Nlinv(args.n, args.coils, use_graph=False, tensor_dft=args.tensor_dft) as ctx:
         rho = torch.from_numpy(fr.rho.astype(np.complex64)).to(dev)
         coils = torch.from_numpy(fr.coils.astype(np.complex64)).to(dev)
         mask = torch.from_numpy(fr.mask).to(dev)
