@@ -522,10 +522,7 @@ def write_traffic(rep: str) -> None:
 def batch_shapes(nframes: int = 64, seed: int = 1004):
     """Seeded uneven workload: grid side from {128, 192, 256, 320, 384}, coils 4..16, spokes 9..31 per frame."""
     from paper_1301_1215_gb300 import synth
-    rng = synth.rng_for(seed)
-    sides = [128, 192, 256, 320, 384]
-    return [(int(sides[rng.integers(0, 5)]), int(rng.integers(4, 17)), int(rng.integers(9, 32)))
-            for _ in range(nframes)]
+    return synth.uneven_batch_shapes(nframes, seed)
 
 
 def frame_bytes(n: int, J: int, newton: int, cg: int) -> float:

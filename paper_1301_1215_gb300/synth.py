@@ -163,6 +163,15 @@ WORKLOADS = {
 }
 
 
+def uneven_batch_shapes(nframes: int = 64, seed: int = 1004):
+    """The uneven batch workload: per frame a grid side from {128, 192, 256, 320, 384}, 4..16 coils and 9..31
+    spokes, drawn from one seeded generator.  Returns [(n, ncoils, spokes)]."""
+    rng = rng_for(seed)
+    sides = [128, 192, 256, 320, 384]
+    return [(int(sides[rng.integers(0, 5)]), int(rng.integers(4, 17)), int(rng.integers(9, 32)))
+            for _ in range(nframes)]
+
+
 @dataclass
 class Frame:
     """Synthetic ground truth and sampling for one frame (image-domain truth, no k-space data)."""
