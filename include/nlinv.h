@@ -252,7 +252,8 @@ NLINV_API nlinv_status nlinv_batch_destroy(nlinv_batch* batch);
 
 /* Waits up to timeout_s seconds (< 0: no limit) for the context's queued work.  ETIMEOUT if it is still running,
  * EBREAKDOWN if a CG breakdown was flagged since the last check (the flag is then cleared), ECUDA on a CUDA
- * error. */
+ * error or when a kernel's wait for its own asynchronous copies or tensor-core stage ran past its time limit (about
+ * a second; the kernel then stopped waiting and its results are not valid). */
 NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
 
 /* Times the kernels of one CG iteration of Eq. 3 with CUDA events on the context's stream, on the workspace left

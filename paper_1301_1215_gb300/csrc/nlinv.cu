@@ -38,6 +38,10 @@ namespace {
 thread_local std::string g_create_error;
 
 // ------------------------------------------------------------------------------------------ vector kernels ----
+// float4 groups of CG-step operands in flight per thread.  Two keep the kernel at 64 registers, four blocks of 256
+// threads per SM; four groups need 96 registers (two blocks per SM, measured 13.2 against 11.5 us per step at
+// 384 x 384 with 10 coils) or spill at 64.
+constexpr int kCgGroups = 2;
 // dx += alpha p; r -= alpha q; partial of |r|^2 -> rr_part[bid], over this block's share of the A.n2 float4.
 // A thread sums the squares of at most two float4 (8 products) in FP32 before adding them to its FP64 partial.
 __device__ __forceinline__ void cg_step_update(float4& d, float4& r, const float4& p, const float4& q, float a,
@@ -47,27 +51,10 @@ __device__ __forceinline__ void cg_step_update(float4& d, float4& r, const float
   acc += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
 }
 
-__device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
-  const float4* __restrict__ p4 = (const float4*)A.p;
-  const float4* __restrict__ q4 = (const float4*)A.q;
-  float4* __restrict__ r4 = (float4*)A.r;
-  float4* __restrict__ dx4 = (float4*)A.dx;
-  // Two groups of operands per thread in flight: the first two are loaded while the block forms
-  // alpha = |r|^2 / Re<p, A p> from the partials of the normal-operator pass (every block sums them in the same
-  // fixed order).  The solve stops at the rounding floor: |r|^2 <= kCgFloor2 |b|^2 (|r| at the FP32 unit roundoff
-  // relative to |b|, including b = 0), Re<p, A p> <= 0 (impossible in exact arithmetic for the positive definite
-  // system of Eq. 3) or a non-finite value.  This step and every later step of the same solve are then empty
-  // (alpha = 0), through a flag latched in the scalars until the next right-hand side, and block 0 records the
-  // iteration.  Non-finite values also set the breakdown flag.  Every block takes the same decision from the same
-  // partials, so a block that already sees the flag set by block 0 in this launch decides as block 0 did.
-  const long stride = (long)nblk * blockDim.x;
-  long i = bid * (long)blockDim.x + threadIdx.x;
-  float4 p0, q0, r0, d0, p1, q1, r1, d1;
-  if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
-  if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
-  __shared__ float s_alpha;
-  __shared__ int s_skip;
-  __shared__ double red[32];
+// The CG step's scalars, the same in every block: t = Re<p, A p> from the n_pq partials, alpha = |r|^2 / t, and the
+// rounding-floor test (see cg_step_body).  Block 0 publishes them; s_alpha and s_skip (stopped by an earlier
+// iteration) are valid for every thread of the block on return.
+__device__ __forceinline__ void cg_step_decide(const KArgs& A, int bid, float& s_alpha, int& s_skip, double* red) {
   double t = 0.0;
   for (int k = threadIdx.x; k < A.n_pq; k += blockDim.x) t += A.pq_part[k];
   t = nlv::block_sum(t, red);
@@ -100,27 +87,166 @@ __device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) 
     s_skip = was_stopped ? 1 : 0;     // stopped by an earlier iteration: nothing to update
   }
   __syncthreads();
+}
+
+template <int G = 2>
+__device__ __forceinline__ void cg_step_body(const KArgs& A, int bid, int nblk) {
+  const float4* __restrict__ p4 = (const float4*)A.p;
+  const float4* __restrict__ q4 = (const float4*)A.q;
+  float4* __restrict__ r4 = (float4*)A.r;
+  float4* __restrict__ dx4 = (float4*)A.dx;
+  // Two groups of operands per thread in flight: the first two are loaded while the block forms
+  // alpha = |r|^2 / Re<p, A p> from the partials of the normal-operator pass (every block sums them in the same
+  // fixed order).  The solve stops at the rounding floor: |r|^2 <= kCgFloor2 |b|^2 (|r| at the FP32 unit roundoff
+  // relative to |b|, including b = 0), Re<p, A p> <= 0 (impossible in exact arithmetic for the positive definite
+  // system of Eq. 3) or a non-finite value.  This step and every later step of the same solve are then empty
+  // (alpha = 0), through a flag latched in the scalars until the next right-hand side, and block 0 records the
+  // iteration.  Non-finite values also set the breakdown flag.  Every block takes the same decision from the same
+  // partials, so a block that already sees the flag set by block 0 in this launch decides as block 0 did.
+  const long stride = (long)nblk * blockDim.x;
+  long i = bid * (long)blockDim.x + threadIdx.x;
+  float4 pg[G], qg[G], rg[G], dg[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g)
+    if (i + g * stride < A.n2) {
+      const long k = i + g * stride;
+      pg[g] = p4[k]; qg[g] = q4[k]; rg[g] = r4[k]; dg[g] = dx4[k];
+    }
+  __shared__ float s_alpha;
+  __shared__ int s_skip;
+  __shared__ double red[32];
+  cg_step_decide(A, bid, s_alpha, s_skip, red);
   if (s_skip) return;                 // the same for the whole block (thread 0 decided for it)
   const float a = s_alpha;
   double accd = 0.0;
+  // G groups in flight per thread; each group's operands for the next round are loaded right after it is stored,
+  // while the other groups of this round are processed
   while (i < A.n2) {
     float acc = 0.f;
-    cg_step_update(d0, r0, p0, q0, a, acc);
-    dx4[i] = d0;
-    r4[i] = r0;
-    const long i1 = i + stride;
-    if (i1 < A.n2) {
-      cg_step_update(d1, r1, p1, q1, a, acc);
-      dx4[i1] = d1;
-      r4[i1] = r1;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const long k = i + g * stride;
+      if (k < A.n2) {
+        cg_step_update(dg[g], rg[g], pg[g], qg[g], a, acc);
+        dx4[k] = dg[g];
+        r4[k] = rg[g];
+        const long kn = k + G * stride;
+        if (kn < A.n2) { pg[g] = p4[kn]; qg[g] = q4[kn]; rg[g] = r4[kn]; dg[g] = dx4[kn]; }
+      }
     }
     accd += (double)acc;
-    i += 2 * stride;
-    if (i < A.n2) { p0 = p4[i]; q0 = q4[i]; r0 = r4[i]; d0 = dx4[i]; }
-    if (i + stride < A.n2) { p1 = p4[i + stride]; q1 = q4[i + stride]; r1 = r4[i + stride]; d1 = dx4[i + stride]; }
+    i += G * stride;
   }
   const double s = nlv::block_sum(accd, red);
   if (threadIdx.x == 0) A.rr_part[bid] = s;
+}
+
+// ------------------------------------------------------------------ CG step with bulk asynchronous copies ----
+// The single-frame CG step as a persistent kernel, one block per SM: the vector is cut into chunks of kBulkChunk
+// float4 per array, and a block's chunks (b, b + nblk, ...) stream p, q, r and dx through a ring of kBulkStages
+// shared-memory stages filled by cp.async.bulk (one thread issues four bulk copies per chunk, completion counted in
+// bytes on the stage's mbarrier), so that up to kBulkStages chunks -- 3 x 64 KB -- are in flight per SM without
+// holding them in registers.  Each thread then updates its share of the chunk from shared memory and stores dx and
+// r directly.  Every wait is bounded (about a second of clock cycles): on a timeout the kernel sets
+// kFlagCopyTimeout, waits once more (bounded) for its copies in flight and returns; the host reports ECUDA.
+constexpr int kBulkThreads = 512;
+constexpr int kBulkChunk = 1024;        // float4 per array per chunk (16 KB)
+constexpr int kBulkStages = 3;
+constexpr size_t kBulkSmem = (size_t)kBulkStages * 4 * kBulkChunk * sizeof(float4) + kBulkStages * 8;
+constexpr int kFlagCopyTimeout = 8;     // Scalars::flags bit: a bulk-copy completion wait timed out
+
+__device__ __forceinline__ uint32_t shared_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Waits (bounded by about a second of clock cycles) for the phase of parity `parity` of the mbarrier at bar.
+__device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+    __nanosleep(20);
+  }
+}
+
+// Thread 0: chunk c of the four arrays into stage s (bytes counted on the stage's barrier).
+__device__ __forceinline__ void bulk_issue(const KArgs& A, float4* ring, uint32_t bar, long c, int s) {
+  const long off = c * kBulkChunk;
+  const long cnt = (A.n2 - off) < kBulkChunk ? (A.n2 - off) : kBulkChunk;
+  const uint32_t bytes = (uint32_t)(cnt * sizeof(float4));
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+               ::"r"(bar), "r"(4u * bytes) : "memory");
+  const float4* src[4] = {(const float4*)A.p, (const float4*)A.q, (const float4*)A.r, (const float4*)A.dx};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const uint32_t dst = shared_addr(ring + ((size_t)s * 4 + a) * kBulkChunk);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src[a] + off), "r"(bytes), "r"(bar) : "memory");
+  }
+}
+
+__global__ void __launch_bounds__(kBulkThreads, 1) cg_step_bulk(const KArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  nlv::pdl_enter();
+  float4* ring = (float4*)smem_raw;
+  const uint32_t bar0 = shared_addr(smem_raw + (size_t)kBulkStages * 4 * kBulkChunk * sizeof(float4));
+  const int bid = blockIdx.x, nblk = gridDim.x;
+  const long nchunks = (A.n2 + kBulkChunk - 1) / kBulkChunk;
+  const long mine = bid < nchunks ? (nchunks - bid + nblk - 1) / nblk : 0;   // chunks bid, bid + nblk, ...
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < kBulkStages; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * st) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const long first = mine < kBulkStages ? mine : kBulkStages;
+  if (threadIdx.x == 0)
+    for (long k = 0; k < first; ++k) bulk_issue(A, ring, bar0 + 8u * (uint32_t)k, bid + k * nblk, (int)k);
+  __shared__ float s_alpha;
+  __shared__ int s_skip;
+  __shared__ double red[32];
+  cg_step_decide(A, bid, s_alpha, s_skip, red);
+  bool timed_out = false;
+  if (s_skip) {                       // stopped earlier: let the copies already issued land, then leave
+    for (long k = 0; k < first; ++k) bulk_wait(bar0 + 8u * (uint32_t)k, 0);
+    return;
+  }
+  const float a = s_alpha;
+  float4* __restrict__ r4 = (float4*)A.r;
+  float4* __restrict__ dx4 = (float4*)A.dx;
+  double accd = 0.0;
+  for (long k = 0; k < mine; ++k) {
+    const int st = (int)(k % kBulkStages);
+    const uint32_t bar = bar0 + 8u * st;
+    if (!bulk_wait(bar, (uint32_t)((k / kBulkStages) & 1))) timed_out = true;
+    const long off = (bid + k * nblk) * kBulkChunk;
+    const long cnt = (A.n2 - off) < kBulkChunk ? (A.n2 - off) : kBulkChunk;
+    const float4* sp = ring + ((size_t)st * 4 + 0) * kBulkChunk;
+    const float4* sq = sp + kBulkChunk;
+    const float4* sr = sq + kBulkChunk;
+    const float4* sd = sr + kBulkChunk;
+    float acc = 0.f;
+    for (long e = threadIdx.x; e < cnt; e += kBulkThreads) {
+      float4 d = sd[e], r = sr[e];
+      cg_step_update(d, r, sp[e], sq[e], a, acc);
+      dx4[off + e] = d;
+      r4[off + e] = r;
+    }
+    accd += (double)acc;
+    __syncthreads();                  // every thread is done with stage st
+    if (threadIdx.x == 0 && k + kBulkStages < mine) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      bulk_issue(A, ring, bar, bid + (k + kBulkStages) * nblk, st);
+    }
+  }
+  if (timed_out) {
+    if (threadIdx.x == 0) atomicOr(&A.sc->flags, kFlagCopyTimeout);
+    for (long k = (mine > kBulkStages ? mine - kBulkStages : 0); k < mine; ++k)
+      bulk_wait(bar0 + 8u * (uint32_t)(k % kBulkStages), (uint32_t)((k / kBulkStages) & 1));
+  }
+  const double sblk = nlv::block_sum(accd, red);
+  if (threadIdx.x == 0) A.rr_part[bid] = sblk;
 }
 
 // x += dx (x = A.dst)
@@ -152,9 +278,11 @@ __global__ void image_kernel(const KArgs A) {
   }
 }
 
-__global__ void cg_step_kernel(const KArgs A) {
+// 256 threads, at most 64 registers: four blocks fit on an SM (the default vector grid)
+template <int G>
+__global__ void __launch_bounds__(256, 4) cg_step_kernel(const KArgs A) {
   nlv::pdl_enter();
-  cg_step_body(A, blockIdx.x, gridDim.x);
+  cg_step_body<G>(A, blockIdx.x, gridDim.x);
 }
 __global__ void add_kernel(const KArgs A) {
   nlv::pdl_enter();
@@ -191,12 +319,15 @@ __global__ void cg_init_kernel(const KArgs A) {
   nlv::grid_reduce(acc, A, blockIdx.x, gridDim.x);
 }
 
-__global__ void cg_step_batch(const nlv::BatchArgs B) {
+// the single-frame CG step
+const void* cg_step_fn() { return (const void*)cg_step_kernel<kCgGroups>; }
+
+__global__ void __launch_bounds__(256, 4) cg_step_batch(const nlv::BatchArgs B) {
   nlv::pdl_enter();
   for (int w = blockIdx.x; w < B.total; w += gridDim.x) {
     int bid, nblk;
     const KArgs& A = nlv::batch_frame(B, w, bid, nblk);
-    cg_step_body(A, bid, nblk);
+    cg_step_body<kCgGroups>(A, bid, nblk);
   }
 }
 __global__ void add_batch(const nlv::BatchArgs B) {
@@ -430,6 +561,10 @@ cudaError_t q_adj_col(nlinv_ctx* c, const float2* x, bool in_cg = false) {
   return col(c, nlv::COL_IFFT_ADJ_FFT, a);
 }
 
+// Blocks of the CG step, i.e. the |r|^2 partials the next iteration's first pass adds: one per SM for the bulk-copy
+// form of single frames, the vector grid for batch frames.
+int cg_blocks(const nlinv_ctx* c) { return c->batch_lanes > 0 ? c->vec_blocks : c->sms; }
+
 // dx += alpha p, r -= alpha q, partials of |r|^2; alpha from the n_pq partials of the normal-operator pass.
 // newton / iter: indices of the Newton step and of the CG iteration (recorded if the solve stops here).
 cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter) {
@@ -446,7 +581,9 @@ cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter) {
   a.dx = c->dx;
   a.n2 = c->vec / 2;
   void* args[] = {&a};
-  return launch(c, (const void*)cg_step_kernel, c->vec_blocks, kVecThreads, 0, args);
+  if (c->batch_lanes > 0)     // batch frames: the register-staged form, which the batched kernel runs
+    return launch(c, cg_step_fn(), c->vec_blocks, kVecThreads, 0, args);
+  return launch(c, (const void*)cg_step_bulk, cg_blocks(c), kBulkThreads, kBulkSmem, args);
 }
 
 // x += dx
@@ -474,7 +611,7 @@ cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
   a.pupd = 1;
   if (!first) {
     a.rr_part = c->rr_part;
-    a.n_rr = c->vec_blocks;
+    a.n_rr = cg_blocks(c);
   }
   a.dst = c->T;
   return row(c, nlv::ROW_W_IFFT, a);
@@ -821,6 +958,7 @@ nlinv_status create_ctx(const nlinv_params* params, void* stream, int batch_lane
     if (smem_err.empty() && c->k->col_std[m]) allow(c->k->col_std[m], c->k->col_smem(m, c->Wc));
     if (smem_err.empty() && c->k->col_std_batch[m]) allow(c->k->col_std_batch[m], c->k->col_smem(m, c->Wc));
   }
+  if (smem_err.empty()) allow((const void*)cg_step_bulk, kBulkSmem);
   if (c->tc) {
     for (int m = 0; m < nlv::NUM_ROW_MODES && smem_err.empty(); ++m) {
       if (c->k->row_tc[m]) allow(c->k->row_tc[m], c->k->row_smem_tc(m, lanes_max));
@@ -1092,10 +1230,10 @@ nlinv_status nlinv_reconstruct(nlinv_ctx* c, const nlinv_c32* y, const uint8_t* 
     NLV_TRY(cudaStreamSynchronize(c->stream), "synchronize");
     if (resid)
       for (int n = 0; n <= c->prm.newton_steps; ++n) resid[n] = hs.resid[n];
-    if (hs.flags & nlv::kFlagTcTimeout) {
+    if (hs.flags & (nlv::kFlagTcTimeout | kFlagCopyTimeout)) {
       int zero = 0;
       cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice);
-      return fail(c, NLINV_ECUDA, "a tensor-core DFT stage did not complete within its time limit");
+      return fail(c, NLINV_ECUDA, "an asynchronous copy or tensor-core stage did not complete within its time limit");
     }
     if (hs.flags & 1) {
       int zero = 0;
@@ -1127,6 +1265,11 @@ nlinv_status nlinv_wait(nlinv_ctx* c, double timeout_s) {
   cudaEventDestroy(ev);
   int flags = 0;
   NLV_TRY(cudaMemcpy(&flags, &c->sc->flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+  if (flags & (nlv::kFlagTcTimeout | kFlagCopyTimeout)) {
+    int zero = 0;
+    NLV_TRY(cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
+    return fail(c, NLINV_ECUDA, "an asynchronous copy or tensor-core stage did not complete within its time limit");
+  }
   if (flags & 1) {
     int zero = 0;
     NLV_TRY(cudaMemcpy(&c->sc->flags, &zero, sizeof(int), cudaMemcpyHostToDevice), "clear flags");
@@ -1586,7 +1729,7 @@ const void* multi_kernel(const SizeKernels* k, const void* fn, size_t* smem) {
     if (k->col_std[m] && fn == k->col_std[m]) { *smem = mk->col_smem[m]; return mk->col_std[m]; }
   }
   *smem = 0;
-  if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
+  if (fn == cg_step_fn()) return (const void*)cg_step_batch;
   if (fn == (const void*)add_kernel) return (const void*)add_batch;
   return nullptr;
 }
@@ -1601,7 +1744,7 @@ const void* batched_kernel(const SizeKernels* k, const void* fn) {
     if (fn == k->col[m]) return k->col_batch[m];
     if (k->col_std[m] && fn == k->col_std[m]) return k->col_std_batch[m];
   }
-  if (fn == (const void*)cg_step_kernel) return (const void*)cg_step_batch;
+  if (fn == cg_step_fn()) return (const void*)cg_step_batch;
   if (fn == (const void*)add_kernel) return (const void*)add_batch;
   return nullptr;
 }

@@ -94,6 +94,7 @@ def test_every_context_call_rejects_a_null_context(lib):
     assert lib.nlinv_autotune(None, None, None, None, 3, None, None, 0) == E
     assert lib.nlinv_set_shapes(None, None) == E
     assert lib.nlinv_cg_stops(None, None, 0) == E
+    assert lib.nlinv_batch_profile_cg(None, 1, ms) == E
     assert lib.nlinv_reconstruct_batch(None, 0, None) == E
     assert lib.nlinv_batch_launch_count(None) == -1
     assert lib.nlinv_batch_destroy(None) == _lib.OK

@@ -111,3 +111,17 @@ def test_batch_at_workload_sizes_matches_single_frames_and_oracle():
             assert rel(xs[i], xo) < 1e-3, (i, n, J)
             assert np.allclose(res[i], ro, rtol=1e-4), (i, n, J)
     assert seen == {128, 192, 256, 320, 384}
+
+
+def test_batch_profile_times_every_cg_kernel(data):
+    """nlinv_batch_profile_cg: one positive duration per CG kernel after a batched reconstruction; refused before."""
+    torch, frames = data
+    from paper_1301_1215_gb300.nlinv import NlinvBatch, NlinvError
+    dev = torch.device("cuda")
+    with NlinvBatch([SHAPES[i][:2] for i in (0, 1)], newton_steps=2, cg_iters=4) as b:
+        with pytest.raises(NlinvError):
+            b.profile_cg(reps=2)
+        b.reconstruct([_t(torch, frames[i][2], dev) for i in (0, 1)],
+                      [_t(torch, frames[i][1].mask, dev) for i in (0, 1)])
+        ms = b.profile_cg(reps=2)
+    assert len(ms) == 6 and all(v > 0 for v in ms.values())

@@ -93,6 +93,21 @@ def test_autotune_picks_a_candidate_and_keeps_parity(torch_cuda):
         assert ctx.autotune(ty, tm, tx, reps=2) == t
 
 
+def test_set_shapes_rejects_what_is_not_compiled(torch_cuda):
+    from paper_1301_1215_gb300 import _lib
+    from paper_1301_1215_gb300.nlinv import Nlinv, NlinvError
+    with Nlinv(384, 4, newton_steps=1, cg_iters=2) as ctx:
+        for bad in [dict(split_n1=8), dict(split_n1=16, col_strip=6), dict(split_n1=16, row_blocks_per_sm=4),
+                    dict(split_n1=16, vec_blocks_per_sm=0)]:
+            with pytest.raises(NlinvError) as ei:
+                ctx.set_shapes(**bad)
+            assert ei.value.status == _lib.EINVAL
+        ctx.set_shapes(16, 8)          # the compiled shapes are always accepted
+    with Nlinv(512, 2, tensor_dft=True, newton_steps=1, cg_iters=2) as ctx:
+        with pytest.raises(NlinvError):
+            ctx.set_shapes(16, 4)      # the tensor-core passes keep the compiled strips
+
+
 @pytest.mark.parametrize("n,split,strip", [(128, 4, 8), (128, 8, 4), (192, 8, 8), (192, 12, 16), (256, 8, 8),
                                            (256, 16, 4), (320, 10, 8), (320, 16, 16), (384, 12, 8), (384, 16, 4),
                                            (384, 16, 16), (512, 16, 4), (512, 16, 16)])
