@@ -17,6 +17,7 @@ TOL = 1e-5
 CASES = [  # (n, J, fov)
     (16, 1, 4), (32, 3, 8), (48, 2, 12), (64, 4, 13), (80, 3, 20), (96, 2, 48), (128, 4, 32), (160, 2, 37),
     (192, 3, 48), (256, 8, 64), (320, 2, 80), (384, 10, 96), (512, 16, 128),
+    (64, 64, 16), (512, 24, 128),      # the largest coil count the interface takes; more coils at the largest side
 ]
 
 

@@ -169,6 +169,26 @@ def test_realtime_series_matches_oracle(torch_cuda):
             assert rel(x.cpu().numpy(), ref[k]) < TOL_X
 
 
+def test_realtime_series_384_matches_oracle(torch_cuda):
+    # the series workload itself: 384 x 384 grid, 10 coils, 13 spokes, 7 Newton x 30 CG, one graph per frame,
+    # frame 1 started from and regularised toward frame 0's result
+    torch = torch_cuda
+    from paper_1301_1215_gb300.nlinv import Nlinv
+    n, J, spokes, frames = 384, 10, 13, 2
+    datas = [noisy_data(n, J, spokes, 1003, frame=k) for k in range(frames)]
+    s = datas[0][0]
+    ys = [d[2].astype(np.complex64).astype(np.complex128) for d in datas]
+    masks = [d[1].mask for d in datas]
+    ref = O.realtime_series(s, masks, ys, synth.initial_guess(n, J), 7, 30)
+    with Nlinv(n, J, newton_steps=7, cg_iters=30) as ctx:
+        x = _t(torch, synth.initial_guess(n, J))
+        for k in range(frames):
+            ctx.reconstruct_inplace(_t(torch, ys[k]), _t(torch, masks[k]), x)
+            xk = x.cpu().numpy()
+            assert rel(xk, ref[k]) < TOL_X
+            assert rel(xk[0], ref[k][0]) < TOL_X
+
+
 def test_host_buffers_give_the_device_result(torch_cuda):
     torch = torch_cuda
     from paper_1301_1215_gb300.nlinv import Nlinv
