@@ -91,6 +91,7 @@ struct KArgs {
   float coef;               // vector passes: second coefficient of out = alpha X + coef Y
   const void* tcB;          // tensor-core passes: the B tiles of the radix-16 DFT stage (tc_dft.cuh)
   int cgskip;               // a launch of the CG iteration: it returns at once when the solve has stopped
+                            // (kCgSkipAfterWait, kCgSkipEarly: see cg_flags_early)
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -110,6 +111,22 @@ __device__ __forceinline__ void pdl_enter() {
 // itself, with no barrier.  (The CG step takes its own decision block-wide, inside cg_step_body.)
 __device__ __forceinline__ bool cg_stopped(const KArgs& A) {
   return A.cgskip && (*(volatile const int*)&A.sc->flags & kFlagCgStopped) != 0;
+}
+
+// cgskip values.  kCgSkipEarly marks a pass whose flag may be read before its dependent-launch wait, so that the
+// read overlaps the kernel before it instead of delaying this pass's first loads.  What a kernel may read before
+// its wait: a kernel is scheduled only once every block of the kernel before it has passed its own wait (pdl_enter:
+// wait, then launch_dependents), i.e. once the kernel two launches back has completed, so anything written two or
+// more launches back (or before the stream reached the library's first kernel) is in place.  For the second to
+// fifth passes of the CG iteration the flag's writer (the previous CG step) is two or more launches back; for the
+// first pass it is the kernel just before.
+constexpr int kCgSkipAfterWait = 1, kCgSkipEarly = 2;
+__device__ __forceinline__ int cg_flags_early(const KArgs& A) {
+  return A.cgskip == kCgSkipEarly ? *(volatile const int*)&A.sc->flags : 0;
+}
+// The stop test of a single-frame pass, given what cg_flags_early read before the wait.
+__device__ __forceinline__ bool cg_stopped_after(const KArgs& A, int early_flags) {
+  return A.cgskip == kCgSkipEarly ? (early_flags & kFlagCgStopped) != 0 : cg_stopped(A);
 }
 
 // ------------------------------------------------------------------------------------------- geometry ----
@@ -355,10 +372,45 @@ __device__ __forceinline__ double rho_slice(const KArgs& A, int bid) {
   return accd;
 }
 
+// Side rows of the round starting at row R0 (sampling pattern, weights, data).  Every launch sequence writes these,
+// if at all, two or more launches before the pass that stages them (the data rows of the gradient's second
+// residual are the first residual, three launches back), never in the launch just before, so that a single-frame
+// pass may stage them before its dependent-launch wait (see cg_flags_early for why that suffices).
+template <int N, int MODE>
+__device__ __forceinline__ void row_stage_side(const KArgs& A, const RowSmem& L, int R0, int r_end, int LANES,
+                                               unsigned char* smem_raw) {
+  using T = RowTraits<MODE>;
+  for (int l = 0; l < LANES; ++l) {
+    const int Rl = R0 + l;
+    if (Rl >= r_end) break;
+    const int e1l = Rl % N;
+    if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
+    if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
+    if constexpr (MODE == ROW_FFT_RESID)
+      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
+  }
+}
+
+// The twiddles and the first round's side rows of a single-frame row pass, issued before its dependent-launch
+// wait (row_pass_body with PRE then skips them).
+template <int N1, int N2, int MODE>
+__device__ __forceinline__ void row_pass_prestage(const KArgs& A, int bid, unsigned char* smem_raw) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N;
+  const int LANES = blockDim.x / S::TL;
+  const RowSmem L = row_smem(MODE, N, LANES, S::SM_LANE);
+  const int r_begin = bid * A.rows_per_cta;
+  const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
+  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  if (r_begin < r_end) row_stage_side<N, MODE>(A, L, r_begin, r_end, LANES, smem_raw);
+}
+
 // Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
-template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc>
+// PRE: the twiddles and the first round's side rows were staged by row_pass_prestage.
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, bool PRE = false>
 __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw,
                                               TC* tc = nullptr) {
   using S = Split<N1, N2>;
@@ -383,8 +435,10 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   const float rs = rsqrtf((float)N);
   const int r_begin = bid * A.rows_per_cta;
   const int r_end = min(r_begin + A.rows_per_cta, A.nrows);
-  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
-  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  if (!PRE) {
+    stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+    stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  }
   __shared__ float s_beta;       // beta of the direction update p = r + beta p (ROW_W_IFFT with pupd)
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
@@ -422,15 +476,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   }
 
   // ---- staged side inputs (the twiddles were issued before the first round)
-  for (int l = 0; l < LANES; ++l) {
-    const int Rl = R0 + l;
-    if (Rl >= r_end) break;
-    const int e1l = Rl % N;
-    if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
-    if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
-    if constexpr (MODE == ROW_FFT_RESID)
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
-  }
+  if (!PRE || R0 != r_begin) row_stage_side<N, MODE>(A, L, R0, r_end, LANES, smem_raw);
   // beta from the |r|^2 partials of the CG step before, while the loads above are in flight (same order in every
   // block; block 0 publishes |r|^2 and beta for the CG step and the later passes of this iteration)
   if constexpr (MODE == ROW_W_IFFT) {
@@ -580,9 +626,14 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 template <int N1, int N2, int MODE, bool STDF = false>
 __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int early = cg_flags_early(A);
+  row_pass_prestage<N1, N2, MODE>(A, blockIdx.x, smem_raw);
   pdl_enter();
-  if (cg_stopped(A)) return;
-  row_pass_body<N1, N2, MODE, STDF>(A, blockIdx.x, gridDim.x, smem_raw);
+  if (cg_stopped_after(A, early)) {
+    cp_async_wait_all();
+    return;
+  }
+  row_pass_body<N1, N2, MODE, STDF, NoTc, true>(A, blockIdx.x, gridDim.x, smem_raw);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----
@@ -646,7 +697,37 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
   }
 }
 
-template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, int CC = NLV_COL_C>
+// The twiddles and the staged side inputs (Omega rows of the block's columns of the coil, rho, drho and r planes)
+// of a column pass.  The launch just before a column pass is a row pass that writes T (and, with the direction
+// update, the coil planes of p, while drho is a rho plane): the side inputs were written two or more launches
+// back, so that a single-frame column pass may stage them before its dependent-launch wait (cg_flags_early).
+template <int N1, int N2, int MODE, bool STDF, int CC>
+__device__ __forceinline__ void col_stage_side(const KArgs& A, int bid, unsigned char* smem_raw) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, C = ColCfg<N1, N2, CC>::C;
+  const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc;
+  const int strips = (Wc + C - 1) / C;
+  const int j = bid / strips;
+  const int cc0 = (bid % strips) * C;
+  const ColSmem L = col_smem(MODE, N, C, S::SM_LANE_COL, Wc);
+  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
+  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
+  if (j < A.nrows) {
+    float2* sd = (float2*)(smem_raw + L.side);
+    const size_t sstride = (size_t)Wc * C;
+    if constexpr (MODE == COL_IFFT_PROD_FFT || MODE == COL_IFFT_ADJ_FFT) {
+      stage_compact_cols(sd, A.coil + (size_t)j * Wc * Wc, cc0, C, Wc);
+      stage_natural_cols(sd + sstride, A.rho, cc0, C, Wc, N, f);
+    }
+    if constexpr (MODE == COL_IFFT_PROD_FFT) {
+      stage_natural_cols(sd + 2 * sstride, A.drho, cc0, C, Wc, N, f);
+      if (A.pupd) stage_natural_cols(sd + 3 * sstride, A.r, cc0, C, Wc, N, f);
+    }
+  }
+}
+
+// PRE: the twiddles and side inputs were staged by col_stage_side before the dependent-launch wait.
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, int CC = NLV_COL_C, bool PRE = false>
 __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw, TC* tc = nullptr) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2, CC>::C;
@@ -687,20 +768,7 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
     }
   }
   // ---- staged side inputs (Omega rows of this block's columns) and twiddles
-  stage_bytes(smem_raw + L.tw, A.twA, N * 8);
-  stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
-  if (j < A.nrows) {
-    float2* sd = (float2*)(smem_raw + L.side);
-    const size_t sstride = (size_t)Wc * C;
-    if constexpr (MODE == COL_IFFT_PROD_FFT || MODE == COL_IFFT_ADJ_FFT) {
-      stage_compact_cols(sd, A.coil + (size_t)j * Wc * Wc, cc0, C, Wc);
-      stage_natural_cols(sd + sstride, A.rho, cc0, C, Wc, N, f);
-    }
-    if constexpr (MODE == COL_IFFT_PROD_FFT) {
-      stage_natural_cols(sd + 2 * sstride, A.drho, cc0, C, Wc, N, f);
-      if (A.pupd) stage_natural_cols(sd + 3 * sstride, A.r, cc0, C, Wc, N, f);
-    }
-  }
+  if (!PRE) col_stage_side<N1, N2, MODE, STDF, CC>(A, bid, smem_raw);
   cp_async_wait_all();
   __syncthreads();
 
@@ -768,9 +836,14 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
 template <int N1, int N2, int MODE, bool STDF = false, int CC = NLV_COL_C>
 __global__ void __launch_bounds__(ColCfg<N1, N2, CC>::THREADS) col_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int early = cg_flags_early(A);
+  col_stage_side<N1, N2, MODE, STDF, CC>(A, blockIdx.x, smem_raw);
   pdl_enter();
-  if (cg_stopped(A)) return;
-  col_pass_body<N1, N2, MODE, STDF, NoTc, CC>(A, blockIdx.x, smem_raw);
+  if (cg_stopped_after(A, early)) {
+    cp_async_wait_all();
+    return;
+  }
+  col_pass_body<N1, N2, MODE, STDF, NoTc, CC, true>(A, blockIdx.x, smem_raw);
 }
 
 // ------------------------------------------------------------------------------- tensor-core passes ----

@@ -552,7 +552,7 @@ cudaError_t q_dir(nlinv_ctx* c, const float2* x, const float2* d) {
 // iteration (skipped once the solve has stopped).
 cudaError_t q_adj_col(nlinv_ctx* c, const float2* x, bool in_cg = false) {
   KArgs a = base_args(c);
-  a.cgskip = in_cg ? 1 : 0;
+  a.cgskip = in_cg ? nlv::kCgSkipEarly : 0;
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -569,7 +569,7 @@ int cg_blocks(const nlinv_ctx* c) { return c->batch_lanes > 0 ? c->vec_blocks : 
 // newton / iter: indices of the Newton step and of the CG iteration (recorded if the solve stops here).
 cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter) {
   KArgs a = base_args(c);
-  a.cgskip = 1;
+  a.cgskip = nlv::kCgSkipAfterWait;
   a.slot = newton;
   a.iter = iter;
   a.pq_part = c->pq_part;
@@ -605,7 +605,7 @@ cudaError_t q_add(nlinv_ctx* c) {
 // The steps are separate functions so that nlinv_profile_cg times exactly what a reconstruction launches.
 cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
   KArgs a = base_args(c);
-  a.cgskip = 1;
+  a.cgskip = nlv::kCgSkipAfterWait;
   a.src = c->p + c->plane;
   a.r = c->r + c->plane;
   a.pupd = 1;
@@ -619,7 +619,7 @@ cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
 
 cudaError_t q_cg_k2(nlinv_ctx* c, const float2* x) {
   KArgs a = base_args(c);
-  a.cgskip = 1;
+  a.cgskip = nlv::kCgSkipEarly;
   a.src = c->T;
   a.dst = c->T;
   a.rho = x;
@@ -632,7 +632,7 @@ cudaError_t q_cg_k2(nlinv_ctx* c, const float2* x) {
 
 cudaError_t q_cg_k3(nlinv_ctx* c) {
   KArgs a = base_args(c);
-  a.cgskip = 1;
+  a.cgskip = nlv::kCgSkipEarly;
   a.src = c->T;
   a.dst = c->T;
   a.mask = c->mask;
@@ -641,7 +641,7 @@ cudaError_t q_cg_k3(nlinv_ctx* c) {
 
 cudaError_t q_cg_k5(nlinv_ctx* c, float alpha) {
   KArgs a = base_args(c);
-  a.cgskip = 1;
+  a.cgskip = nlv::kCgSkipEarly;
   a.src = c->T;
   a.dst = c->q;
   a.p = c->p;
