@@ -92,6 +92,8 @@ struct KArgs {
   const void* tcB;          // tensor-core passes: the B tiles of the radix-16 DFT stage (tc_dft.cuh)
   int cgskip;               // a launch of the CG iteration: it returns at once when the solve has stopped
                             // (kCgSkipAfterWait, kCgSkipEarly: see cg_flags_early)
+  int src_early;            // single-frame row passes: src was written two or more launches back, so the first
+                            // round's main loads may be issued before the dependent-launch wait
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -409,10 +411,12 @@ __device__ __forceinline__ void row_pass_prestage(const KArgs& A, int bid, unsig
 // Row pass: block b takes the coil rows [b*rows_per_cta, (b+1)*rows_per_cta) of the stacked J*N rows, one lane
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
-// PRE: the twiddles and the first round's side rows were staged by row_pass_prestage.
+// PRE: the twiddles and the first round's side rows were staged by row_pass_prestage, and the body itself waits for
+// the kernel before (pdl_enter) and applies the stop test: before its first loads, or, with src_early, right after
+// the first round's main loads are issued.
 template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, bool PRE = false>
 __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw,
-                                              TC* tc = nullptr) {
+                                              TC* tc = nullptr, int early_flags = 0) {
   using S = Split<N1, N2>;
   using T = RowTraits<MODE>;
   constexpr int N = S::N, TL = S::TL, E = S::E;
@@ -440,6 +444,18 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
     stage_bytes(smem_raw + L.tw + N * 8, A.twB, N * 8);
   }
   __shared__ float s_beta;       // beta of the direction update p = r + beta p (ROW_W_IFFT with pupd)
+  bool waited = !PRE;
+  // the dependent-launch wait and the stop test (the same for every thread of the block); true: leave the pass
+  auto enter = [&]() -> bool {
+    pdl_enter();
+    waited = true;
+    if (cg_stopped_after(A, early_flags)) {
+      cp_async_wait_all();
+      return true;
+    }
+    return false;
+  };
+  if (PRE && !A.src_early && enter()) return;
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
@@ -449,7 +465,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 
   // ---- direction update: the rows of r go to the exchange buffer (natural order, pitch N) while p is loaded
   if constexpr (MODE == ROW_W_IFFT) {
-    if (A.pupd) {
+    if (A.pupd && waited) {
       for (int l = 0; l < LANES && R0 + l < r_end; ++l)
         stage_bytes(smem_raw + L.xch + (size_t)l * N * 8, A.r + (size_t)(R0 + l) * N, N * 8);
     }
@@ -472,6 +488,15 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
         }
       }
       v[m] = val;
+    }
+  }
+  if (!waited) {                 // src_early: the main loads are in flight; now the inputs of the kernel before
+    if (enter()) return;
+    if constexpr (MODE == ROW_W_IFFT) {
+      if (A.pupd) {
+        for (int l = 0; l < LANES && R0 + l < r_end; ++l)
+          stage_bytes(smem_raw + L.xch + (size_t)l * N * 8, A.r + (size_t)(R0 + l) * N, N * 8);
+      }
     }
   }
 
@@ -628,12 +653,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, kRowCtasPerSM) row_pass(const 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int early = cg_flags_early(A);
   row_pass_prestage<N1, N2, MODE>(A, blockIdx.x, smem_raw);
-  pdl_enter();
-  if (cg_stopped_after(A, early)) {
-    cp_async_wait_all();
-    return;
-  }
-  row_pass_body<N1, N2, MODE, STDF, NoTc, true>(A, blockIdx.x, gridDim.x, smem_raw);
+  row_pass_body<N1, N2, MODE, STDF, NoTc, true>(A, blockIdx.x, gridDim.x, smem_raw, nullptr, early);
 }
 
 // --------------------------------------------------------------------------------------- column passes ----

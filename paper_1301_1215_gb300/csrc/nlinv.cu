@@ -603,7 +603,9 @@ cudaError_t q_add(nlinv_ctx* c) {
 //   K3 row  PSF;  K4 col  adjoint products;  K5 row  q = DF^H DF p + alpha p, p_rho written, Re<p, q> partials
 //   K6      alpha from the K5 partials; dx += alpha p, r -= alpha q, per-block partials of |r|^2
 // The steps are separate functions so that nlinv_profile_cg times exactly what a reconstruction launches.
-cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
+// early: p may be loaded before the dependent-launch wait (false for back-to-back launches of this pass alone,
+// where each launch would read what the one before writes)
+cudaError_t q_cg_k1(nlinv_ctx* c, bool first, bool early = true) {
   KArgs a = base_args(c);
   a.cgskip = nlv::kCgSkipAfterWait;
   a.src = c->p + c->plane;
@@ -612,6 +614,9 @@ cudaError_t q_cg_k1(nlinv_ctx* c, bool first) {
   if (!first) {
     a.rr_part = c->rr_part;
     a.n_rr = cg_blocks(c);
+    // p's coil planes were written by this pass one iteration back (before the first iteration, by the
+    // right-hand side pass just before it)
+    a.src_early = early ? 1 : 0;
   }
   a.dst = c->T;
   return row(c, nlv::ROW_W_IFFT, a);
@@ -1422,7 +1427,7 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
   // duration (consecutive launches overlap ramp and drain through the dependent launch, as in a graph replay)
   auto one = [&](int k) -> cudaError_t {
     switch (k) {
-      case 0: return q_cg_k1(c, false);
+      case 0: return q_cg_k1(c, false, false);
       case 1: return q_cg_k2(c, c->x);
       case 2: return q_cg_k3(c);
       case 3: return q_adj_col(c, c->x, true);
