@@ -260,9 +260,9 @@ NLINV_API nlinv_status nlinv_wait(nlinv_ctx* ctx, double timeout_s);
  * by the last nlinv_reconstruct (whose CG state it advances -- a solve that had stopped at its rounding floor is
  * marked running again, so that every kernel does its full work; x is not changed): each kernel is launched reps times
  * back to back between two events, so ms_out gets its steady-state launch duration (consecutive launches overlap
- * their ramp and drain, as the passes of a graph replay do; the first one issues its loads of p after its wait
- * here, since back to back each launch would read the p the one before writes, while in a reconstruction it
- * issues them before).  With reps = 1 the six kernels run once each, in order.  ms_out (HOST, 6 doubles) receives the mean duration in milliseconds of, in order:
+ * their ramp and drain, as the passes of a graph replay do; the first one and the CG step issue their loads of p, r and
+ * dx after their wait here, since back to back each launch would read what the one before writes, while in a
+ * reconstruction they issue them before).  With reps = 1 the six kernels run once each, in order.  ms_out (HOST, 6 doubles) receives the mean duration in milliseconds of, in order:
  *   [0] row pass  p = r + beta p, W^-1 (first axis)   [1] column pass  W^-1, C (products), FFT
  *   [2] row pass  PSF                                  [3] column pass  FFT^-1, C^H (channel products), FFT
  *   [4] row pass  W^-H + alpha p, Re<p, q>             [5] CG step  dx += alpha p, r -= alpha q, |r|^2

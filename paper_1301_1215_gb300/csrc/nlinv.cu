@@ -170,30 +170,42 @@ __device__ __forceinline__ bool bulk_wait(uint32_t bar, uint32_t parity) {
   }
 }
 
-// Thread 0: chunk c of the four arrays into stage s (bytes counted on the stage's barrier).
-__device__ __forceinline__ void bulk_issue(const KArgs& A, float4* ring, uint32_t bar, long c, int s) {
+// Bytes per array of chunk c.
+__device__ __forceinline__ uint32_t bulk_bytes(const KArgs& A, long c) {
   const long off = c * kBulkChunk;
-  const long cnt = (A.n2 - off) < kBulkChunk ? (A.n2 - off) : kBulkChunk;
-  const uint32_t bytes = (uint32_t)(cnt * sizeof(float4));
+  return (uint32_t)(((A.n2 - off) < kBulkChunk ? (A.n2 - off) : kBulkChunk) * sizeof(float4));
+}
+// Thread 0: the stage's barrier expects the four arrays of chunk c (one arrival with their byte count).
+__device__ __forceinline__ void bulk_expect(const KArgs& A, uint32_t bar, long c) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
-               ::"r"(bar), "r"(4u * bytes) : "memory");
-  const float4* src[4] = {(const float4*)A.p, (const float4*)A.q, (const float4*)A.r, (const float4*)A.dx};
+               ::"r"(bar), "r"(4u * bulk_bytes(A, c)) : "memory");
+}
+// Thread 0: array a (0 p, 1 q, 2 r, 3 dx) of chunk c into stage s, completion counted on the stage's barrier.
+__device__ __forceinline__ void bulk_copy(const KArgs& A, float4* ring, uint32_t bar, long c, int s, int a) {
+  const float4* src = (const float4*)(a == 0 ? A.p : a == 1 ? A.q : a == 2 ? A.r : A.dx);
+  const uint32_t dst = shared_addr(ring + ((size_t)s * 4 + a) * kBulkChunk);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src + c * kBulkChunk), "r"(bulk_bytes(A, c)), "r"(bar) : "memory");
+}
+// Thread 0: chunk c of the four arrays into stage s.
+__device__ __forceinline__ void bulk_issue(const KArgs& A, float4* ring, uint32_t bar, long c, int s) {
+  bulk_expect(A, bar, c);
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const uint32_t dst = shared_addr(ring + ((size_t)s * 4 + a) * kBulkChunk);
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src[a] + off), "r"(bytes), "r"(bar) : "memory");
-  }
+  for (int a = 0; a < 4; ++a) bulk_copy(A, ring, bar, c, s, a);
 }
 
+// With src_early, the first stages' copies of r, dx and of p beyond its rho plane are issued before the
+// dependent-launch wait: the kernel before (the normal-operator pass) writes q and the rho plane of p, and r, dx and
+// the coil planes of p were written two or more launches back (see cg_flags_early in kernels.cuh); q and the rest
+// of p follow the wait.  Without it (back-to-back launches of this kernel alone) every copy follows the wait.
 __global__ void __launch_bounds__(kBulkThreads, 1) cg_step_bulk(const KArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  nlv::pdl_enter();
   float4* ring = (float4*)smem_raw;
   const uint32_t bar0 = shared_addr(smem_raw + (size_t)kBulkStages * 4 * kBulkChunk * sizeof(float4));
   const int bid = blockIdx.x, nblk = gridDim.x;
   const long nchunks = (A.n2 + kBulkChunk - 1) / kBulkChunk;
   const long mine = bid < nchunks ? (nchunks - bid + nblk - 1) / nblk : 0;   // chunks bid, bid + nblk, ...
+  const long rho4 = A.src_early ? (long)A.N * A.N / 2 : A.n2;   // float4 of the rho plane (src_early = 0: all)
   if (threadIdx.x == 0) {
     for (int st = 0; st < kBulkStages; ++st)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8u * st) : "memory");
@@ -201,8 +213,31 @@ __global__ void __launch_bounds__(kBulkThreads, 1) cg_step_bulk(const KArgs A) {
   }
   __syncthreads();
   const long first = mine < kBulkStages ? mine : kBulkStages;
-  if (threadIdx.x == 0)
-    for (long k = 0; k < first; ++k) bulk_issue(A, ring, bar0 + 8u * (uint32_t)k, bid + k * nblk, (int)k);
+  if (threadIdx.x == 0) {
+    for (long k = 0; k < first; ++k) {
+      const long ch = bid + k * nblk;
+      const uint32_t bar = bar0 + 8u * (uint32_t)k;
+      bulk_expect(A, bar, ch);
+      if (A.src_early) {
+        bulk_copy(A, ring, bar, ch, (int)k, 2);
+        bulk_copy(A, ring, bar, ch, (int)k, 3);
+      }
+      if (ch * kBulkChunk >= rho4) bulk_copy(A, ring, bar, ch, (int)k, 0);
+    }
+  }
+  nlv::pdl_enter();
+  if (threadIdx.x == 0) {
+    for (long k = 0; k < first; ++k) {
+      const long ch = bid + k * nblk;
+      const uint32_t bar = bar0 + 8u * (uint32_t)k;
+      bulk_copy(A, ring, bar, ch, (int)k, 1);
+      if (ch * kBulkChunk < rho4) bulk_copy(A, ring, bar, ch, (int)k, 0);
+      if (!A.src_early) {
+        bulk_copy(A, ring, bar, ch, (int)k, 2);
+        bulk_copy(A, ring, bar, ch, (int)k, 3);
+      }
+    }
+  }
   __shared__ float s_alpha;
   __shared__ int s_skip;
   __shared__ double red[32];
@@ -567,9 +602,10 @@ int cg_blocks(const nlinv_ctx* c) { return c->batch_lanes > 0 ? c->vec_blocks : 
 
 // dx += alpha p, r -= alpha q, partials of |r|^2; alpha from the n_pq partials of the normal-operator pass.
 // newton / iter: indices of the Newton step and of the CG iteration (recorded if the solve stops here).
-cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter) {
+cudaError_t q_cg_step(nlinv_ctx* c, int n_pq, int newton, int iter, bool early = true) {
   KArgs a = base_args(c);
   a.cgskip = nlv::kCgSkipAfterWait;
+  a.src_early = early ? 1 : 0;
   a.slot = newton;
   a.iter = iter;
   a.pq_part = c->pq_part;
@@ -1432,7 +1468,7 @@ nlinv_status nlinv_profile_cg(nlinv_ctx* c, int reps, double* ms_out) {
       case 2: return q_cg_k3(c);
       case 3: return q_adj_col(c, c->x, true);
       case 4: return q_cg_k5(c, al);
-      default: return q_cg_step(c, row_geom(c, true).blocks, 0, 0);
+      default: return q_cg_step(c, row_geom(c, true).blocks, 0, 0, false);
     }
   };
   cudaError_t e = cudaSuccess;
