@@ -92,8 +92,8 @@ struct KArgs {
   const void* tcB;          // tensor-core passes: the B tiles of the radix-16 DFT stage (tc_dft.cuh)
   int cgskip;               // a launch of the CG iteration: it returns at once when the solve has stopped
                             // (kCgSkipAfterWait, kCgSkipEarly: see cg_flags_early)
-  int src_early;            // single-frame row passes: src was written two or more launches back, so the first
-                            // round's main loads may be issued before the dependent-launch wait
+  int src_early;            // inputs written two or more launches back, read before the dependent-launch wait:
+                            // the first CG pass's p (its first round's main loads), the CG step's r, dx and p
 };
 
 // ------------------------------------------------------------------------------- dependent launches ----
@@ -412,8 +412,8 @@ __device__ __forceinline__ void row_pass_prestage(const KArgs& A, int bid, unsig
 // (TL threads) per row, in as many rounds as its lanes need; passes with a rho part then take a slice of the rho
 // plane.  All threads of the block run every round (inactive lanes carry zeros) because of the barriers.
 // PRE: the twiddles and the first round's side rows were staged by row_pass_prestage, and the body itself waits for
-// the kernel before (pdl_enter) and applies the stop test: before its first loads, or, with src_early, right after
-// the first round's main loads are issued.
+// the kernel before (pdl_enter) and applies the stop test: before its first loads, or, for the first CG pass with
+// src_early, right after the first round's main loads are issued.
 template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, bool PRE = false>
 __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk, unsigned char* smem_raw,
                                               TC* tc = nullptr, int early_flags = 0) {
@@ -455,7 +455,9 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
     }
     return false;
   };
-  if (PRE && !A.src_early && enter()) return;
+  // with src_early the first CG pass issues its main loads (p) before the wait; every other pass waits first
+  const bool early_main = PRE && MODE == ROW_W_IFFT && A.src_early;
+  if (PRE && !early_main && enter()) return;
 
   for (int R0 = r_begin; R0 < r_end; R0 += LANES) {
   const int RA = R0 + laneA, RB = R0 + laneB;               // rows of the stacked coil planes in the two maps
@@ -481,7 +483,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
         if constexpr (T::load_compact) {
           if (in_omega(e2, N, f)) val = A.src[(size_t)RA * Wc + to_compact(e2, N, f)];
         } else if constexpr (MODE == ROW_W_IFFT) {
-          val = A.src[(size_t)RA * N + e2];
+          val = __ldcg(A.src + (size_t)RA * N + e2);     // from L2 (issued before the wait with src_early)
         } else {  // ROW_P_IFFT
           const float2 sv = A.src[(size_t)RA * N + e2];
           val = A.mask[(size_t)e1A * N + e2] ? sv : make_float2(0.f, 0.f);
@@ -746,9 +748,10 @@ __device__ __forceinline__ void col_stage_side(const KArgs& A, int bid, unsigned
   }
 }
 
-// PRE: the twiddles and side inputs were staged by col_stage_side before the dependent-launch wait.
-template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, int CC = NLV_COL_C, bool PRE = false>
-__device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw, TC* tc = nullptr) {
+// prestaged: the twiddles and side inputs were staged by col_stage_side before the dependent-launch wait.
+template <int N1, int N2, int MODE, bool STDF = false, class TC = NoTc, int CC = NLV_COL_C>
+__device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned char* smem_raw, TC* tc = nullptr,
+                                              bool prestaged = false) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, E = S::E, C = ColCfg<N1, N2, CC>::C;
   const int lane = threadIdx.x % C, idx = threadIdx.x / C;
@@ -788,7 +791,7 @@ __device__ __forceinline__ void col_pass_body(const KArgs& A, int bid, unsigned 
     }
   }
   // ---- staged side inputs (Omega rows of this block's columns) and twiddles
-  if (!PRE) col_stage_side<N1, N2, MODE, STDF, CC>(A, bid, smem_raw);
+  if (!prestaged) col_stage_side<N1, N2, MODE, STDF, CC>(A, bid, smem_raw);
   cp_async_wait_all();
   __syncthreads();
 
@@ -857,13 +860,16 @@ template <int N1, int N2, int MODE, bool STDF = false, int CC = NLV_COL_C>
 __global__ void __launch_bounds__(ColCfg<N1, N2, CC>::THREADS) col_pass(const KArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int early = cg_flags_early(A);
-  col_stage_side<N1, N2, MODE, STDF, CC>(A, blockIdx.x, smem_raw);
+  // before the wait only through L2 (16-byte copies): an odd f stages the natural planes with 8-byte copies,
+  // which go through L1, after the wait
+  const bool pre = STDF || (A.f & 1) == 0;
+  if (pre) col_stage_side<N1, N2, MODE, STDF, CC>(A, blockIdx.x, smem_raw);
   pdl_enter();
   if (cg_stopped_after(A, early)) {
     cp_async_wait_all();
     return;
   }
-  col_pass_body<N1, N2, MODE, STDF, NoTc, CC, true>(A, blockIdx.x, smem_raw);
+  col_pass_body<N1, N2, MODE, STDF, NoTc, CC>(A, blockIdx.x, smem_raw, nullptr, pre);
 }
 
 // ------------------------------------------------------------------------------- tensor-core passes ----
