@@ -245,6 +245,20 @@ __device__ __forceinline__ void stage_bytes(void* sdst, const void* gsrc, int nb
 
 __host__ __device__ constexpr size_t align16(size_t v) { return (v + 15) / 16 * 16; }
 
+// Rows R0 .. R0+nr-1 of rb bytes each (rb a multiple of 16) into consecutive rows of sdst: row R of gsrc, or row
+// R mod N with `wrap` (tables of one plane shared by all coil planes); every run of consecutive source rows is one
+// flat copy, so a thread issues about nr*rb / (16*blockDim.x) copies instead of one loop per row.
+__device__ __forceinline__ void stage_rows(unsigned char* sdst, const void* gsrc, int R0, int nr, int rb, int N,
+                                           bool wrap) {
+  for (int l = 0; l < nr;) {
+    const int R = R0 + l;
+    const int e = wrap ? R % N : R;
+    const int run = wrap ? min(nr - l, N - e) : nr - l;
+    stage_bytes(sdst + (size_t)l * rb, (const unsigned char*)gsrc + (size_t)e * rb, run * rb);
+    l += run;
+  }
+}
+
 // ------------------------------------------------------------------------------------------ row passes ----
 enum RowMode : int {
   ROW_W_IFFT = 0,        // T <- compact cols of FFT^-1_row(w * src / sqrt N)            (W^-1, first axis)
@@ -382,15 +396,10 @@ template <int N, int MODE>
 __device__ __forceinline__ void row_stage_side(const KArgs& A, const RowSmem& L, int R0, int r_end, int LANES,
                                                unsigned char* smem_raw) {
   using T = RowTraits<MODE>;
-  for (int l = 0; l < LANES; ++l) {
-    const int Rl = R0 + l;
-    if (Rl >= r_end) break;
-    const int e1l = Rl % N;
-    if constexpr (T::s_mask) stage_bytes(smem_raw + L.mask + (size_t)l * N, A.mask + (size_t)e1l * N, N);
-    if constexpr (T::s_w) stage_bytes(smem_raw + L.w + (size_t)l * N * 4, A.wtab + (size_t)e1l * N, N * 4);
-    if constexpr (MODE == ROW_FFT_RESID)
-      stage_bytes(smem_raw + L.cplx + (size_t)l * N * 8, A.y + (size_t)Rl * N, N * 8);
-  }
+  const int nr = min(LANES, r_end - R0);
+  if constexpr (T::s_mask) stage_rows(smem_raw + L.mask, A.mask, R0, nr, N, N, true);
+  if constexpr (T::s_w) stage_rows(smem_raw + L.w, A.wtab, R0, nr, N * 4, N, true);
+  if constexpr (MODE == ROW_FFT_RESID) stage_rows(smem_raw + L.cplx, A.y, R0, nr, N * 8, N, false);
 }
 
 // The twiddles and the first round's side rows of a single-frame row pass, issued before its dependent-launch
@@ -467,10 +476,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
 
   // ---- direction update: the rows of r go to the exchange buffer (natural order, pitch N) while p is loaded
   if constexpr (MODE == ROW_W_IFFT) {
-    if (A.pupd && waited) {
-      for (int l = 0; l < LANES && R0 + l < r_end; ++l)
-        stage_bytes(smem_raw + L.xch + (size_t)l * N * 8, A.r + (size_t)(R0 + l) * N, N * 8);
-    }
+    if (A.pupd && waited) stage_rows(smem_raw + L.xch, A.r, R0, min(LANES, r_end - R0), N * 8, N, false);
   }
 
   // ---- main loads, layout A: thread a < N1 holds row elements a + N1*m (no stores until all are issued)
@@ -495,10 +501,7 @@ __device__ __forceinline__ void row_pass_body(const KArgs& A, int bid, int nblk,
   if (!waited) {                 // src_early: the main loads are in flight; now the inputs of the kernel before
     if (enter()) return;
     if constexpr (MODE == ROW_W_IFFT) {
-      if (A.pupd) {
-        for (int l = 0; l < LANES && R0 + l < r_end; ++l)
-          stage_bytes(smem_raw + L.xch + (size_t)l * N * 8, A.r + (size_t)(R0 + l) * N, N * 8);
-      }
+      if (A.pupd) stage_rows(smem_raw + L.xch, A.r, R0, min(LANES, r_end - R0), N * 8, N, false);
     }
   }
 
