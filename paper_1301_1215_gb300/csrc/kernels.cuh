@@ -694,25 +694,25 @@ template <int N1, int N2, int CC = NLV_COL_C> struct ColCfg {
   static_assert(C % 2 == 0, "column staging copies pairs of complex values");
 };
 
-// Stages Omega rows of C columns starting at compact column cc0 of a compact (Wc x Wc per coil) array.
+// Stages Omega rows of C columns starting at compact column cc0 of a compact (Wc x Wc per coil) array.  A thread
+// keeps one 16-byte pair of columns (blockDim.x is a multiple of C/2) and steps down the rows.
 __device__ __forceinline__ void stage_compact_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc) {
   const int cpr = C / 2;                               // 16-byte chunks per row segment
-  for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
-    const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
-    if (cc < Wc) cp_async16(sdst + (size_t)cr * C + 2 * k, plane + (size_t)cr * Wc + cc);
-  }
+  const int k = threadIdx.x % cpr, cc = cc0 + 2 * k, step = blockDim.x / cpr;
+  if (cc >= Wc) return;
+  const float2* src = plane + cc;
+  for (int cr = threadIdx.x / cpr; cr < Wc; cr += step) cp_async16(sdst + (size_t)cr * C + 2 * k, src + (size_t)cr * Wc);
 }
 // Same for a natural N x N plane (rows and columns mapped from compact to natural indices).
 __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* plane, int cc0, int C, int Wc, int N,
                                                    int f) {
   if ((f & 1) == 0) {                                  // compact pairs (2k, 2k+1) stay adjacent in natural order
     const int cpr = C / 2;
-    for (int i = threadIdx.x; i < Wc * cpr; i += blockDim.x) {
-      const int cr = i / cpr, k = i % cpr, cc = cc0 + 2 * k;
-      if (cc < Wc)
-        cp_async16(sdst + (size_t)cr * C + 2 * k,
-                   plane + (size_t)to_natural(cr, N, f) * N + to_natural(cc, N, f));
-    }
+    const int k = threadIdx.x % cpr, cc = cc0 + 2 * k, step = blockDim.x / cpr;
+    if (cc >= Wc) return;
+    const float2* src = plane + to_natural(cc, N, f);
+    for (int cr = threadIdx.x / cpr; cr < Wc; cr += step)
+      cp_async16(sdst + (size_t)cr * C + 2 * k, src + (size_t)to_natural(cr, N, f) * N);
   } else {
     for (int i = threadIdx.x; i < Wc * C; i += blockDim.x) {
       const int cr = i / C, k = i % C, cc = cc0 + k;
@@ -722,10 +722,6 @@ __device__ __forceinline__ void stage_natural_cols(float2* sdst, const float2* p
   }
 }
 
-// The twiddles and the staged side inputs (Omega rows of the block's columns of the coil, rho, drho and r planes)
-// of a column pass.  The launch just before a column pass is a row pass that writes T (and, with the direction
-// update, the coil planes of p, while drho is a rho plane): the side inputs were written two or more launches
-// back, so that a single-frame column pass may stage them before its dependent-launch wait (cg_flags_early).
 template <int N1, int N2, int MODE, bool STDF, int CC>
 __device__ __forceinline__ void col_stage_side(const KArgs& A, int bid, unsigned char* smem_raw) {
   using S = Split<N1, N2>;
