@@ -147,13 +147,30 @@ def test_binding_refuses_without_gpu():
 
 def test_every_kernel_waits_for_its_predecessor():
     # Passes are launched with programmatic stream serialisation, so each kernel must execute
-    # griddepcontrol.wait (nlv::pdl_enter) before touching global memory written by the pass before it.
+    # griddepcontrol.wait (nlv::pdl_enter) before it reads what the kernel just before it wrote, and before
+    # any store.  A kernel may stage inputs written two or more launches back before the wait, so the wait need
+    # not be its first statement; it must be in the kernel's own body, or in row_pass_body, whose PRE form waits
+    # inside its `enter` step (before the first round's stores).
     csrc = os.path.join(ROOT, "paper_1301_1215_gb300", "csrc")
+    kernels = 0
     for name in os.listdir(csrc):
         if not name.endswith((".cu", ".cuh")):
             continue
         lines = open(os.path.join(csrc, name)).read().splitlines()
         for i, line in enumerate(lines):
             if "__global__" in line and "(" in line and line.rstrip().endswith("{"):
-                body = "\n".join(lines[i + 1: i + 5])
-                assert "pdl_enter()" in body, f"{name}:{i + 1} kernel does not start with pdl_enter()"
+                j = i + 1
+                while j < len(lines) and lines[j].rstrip() != "}":
+                    j += 1
+                body = "\n".join(lines[i + 1: j])
+                kernels += 1
+                waits = "pdl_enter()" in body or re.search(r"row_pass_body<[^>]*,\s*true>", body)
+                assert waits, f"{name}:{i + 1} kernel never reaches pdl_enter()"
+    assert kernels >= 10
+    src = open(os.path.join(csrc, "kernels.cuh")).read()
+    body = src[src.index("void row_pass_body("):src.index("__global__ void __launch_bounds__(kRowMaxThreads, "
+                                                          "kRowCtasPerSM) row_pass(")]
+    enter = body[body.index("auto enter = [&]"):]
+    assert "pdl_enter();" in enter[:200]
+    # the deferred wait of the early-load path comes before the first store of a round
+    assert body.index("if (!waited)") < body.index("A.dst[")
