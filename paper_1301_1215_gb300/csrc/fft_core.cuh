@@ -241,7 +241,9 @@ struct NoTc {
 // step 3 on those with out_ok (index out_idx < P2, area sm_out).
 // tc: with an enabled tensor-core engine, a radix-16 register DFT (step 1 when P2 = 16, step 3 when P1 = 16) runs
 // as one block-wide tensor-core contraction instead (every thread takes part; threads without data pass zeros).
-template <int P1, int P2, int D, int E, class TC = NoTc>
+// TRAIL = false drops the closing barrier (CUDA-core stages only): for the last exchange of a pass, when every
+// later write to the exchange area comes after another block-wide barrier (the next round's or work item's).
+template <int P1, int P2, int D, int E, class TC = NoTc, bool TRAIL = true>
 __device__ __forceinline__ void fft_AtoB2(float2 (&v)[E], float2* sm_in, int in_idx, bool in_ok, float2* sm_out,
                                           int out_idx, bool out_ok, const float2* tw, TC* tc = nullptr) {
   constexpr int S = P1 + 1;
@@ -263,12 +265,12 @@ __device__ __forceinline__ void fft_AtoB2(float2 (&v)[E], float2* sm_in, int in_
     if constexpr (!tc3) RegDFT<P1, D>::run(v);
   }
   if constexpr (tc3) tc->template dft16<D>(v, out_ok);
-  __syncthreads();
+  if constexpr (TRAIL || TC::enabled) __syncthreads();
 }
 
-template <int P1, int P2, int D, int E, class TC = NoTc>
+template <int P1, int P2, int D, bool TRAIL = true, int E, class TC = NoTc>
 __device__ __forceinline__ void fft_AtoB(float2 (&v)[E], float2* sm, const float2* tw, int idx, TC* tc = nullptr) {
-  fft_AtoB2<P1, P2, D>(v, sm, idx, idx < P1, sm, idx, idx < P2, tw, tc);
+  fft_AtoB2<P1, P2, D, E, TC, TRAIL>(v, sm, idx, idx < P1, sm, idx, idx < P2, tw, tc);
 }
 
 }  // namespace nlv
