@@ -33,6 +33,7 @@ MultiKernels make_multi() {
   m.col[COL_SIM_FFT] = (const void*)col_pass_multi<COL_SIM_FFT, false>;
   m.col[COL_IFFT_PROD_FFT] = (const void*)col_pass_multi<COL_IFFT_PROD_FFT, false>;
   m.col[COL_IFFT_ADJ_FFT] = (const void*)col_pass_multi<COL_IFFT_ADJ_FFT, false>;
+  m.row_std[ROW_W_IFFT] = (const void*)row_pass_multi<ROW_W_IFFT, true>;
   m.row_std[ROW_PSF] = (const void*)row_pass_multi<ROW_PSF, true>;
   m.row_std[ROW_FFT_W_NORMAL] = (const void*)row_pass_multi<ROW_FFT_W_NORMAL, true>;
   m.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass_multi<COL_IFFT_PROD_FFT, true>;

@@ -1151,6 +1151,7 @@ template <int N1, int N2> SizeKernels make_size_kernels_single() {
   s.col[COL_SIM_FFT] = (const void*)col_pass<N1, N2, COL_SIM_FFT>;
   s.col[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT>;
   s.col[COL_IFFT_ADJ_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_ADJ_FFT>;
+  s.row_std[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT, true>;
   s.row_std[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF, true>;
   s.row_std[ROW_FFT_W_NORMAL] = (const void*)row_pass<N1, N2, ROW_FFT_W_NORMAL, true>;
   s.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, true>;
@@ -1192,11 +1193,13 @@ template <int N1, int N2> SizeKernels make_size_kernels() {
   s.col_batch[COL_SIM_FFT] = (const void*)col_pass_batch<N1, N2, COL_SIM_FFT>;
   s.col_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT>;
   s.col_batch[COL_IFFT_ADJ_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_ADJ_FFT>;
-  // measured: the PSF and normal-operator row passes and the DF column pass gain from the constant field of
-  // view; the p-update row pass and the DF^H column pass do not
+  // measured: the p-update, PSF and normal-operator row passes and the DF column pass gain from the constant
+  // field of view (the batched p-update pass also stops spilling); the DF^H column pass does not
+  s.row_std[ROW_W_IFFT] = (const void*)row_pass<N1, N2, ROW_W_IFFT, true>;
   s.row_std[ROW_PSF] = (const void*)row_pass<N1, N2, ROW_PSF, true>;
   s.row_std[ROW_FFT_W_NORMAL] = (const void*)row_pass<N1, N2, ROW_FFT_W_NORMAL, true>;
   s.col_std[COL_IFFT_PROD_FFT] = (const void*)col_pass<N1, N2, COL_IFFT_PROD_FFT, true>;
+  s.row_std_batch[ROW_W_IFFT] = (const void*)row_pass_batch<N1, N2, ROW_W_IFFT, true>;
   s.row_std_batch[ROW_PSF] = (const void*)row_pass_batch<N1, N2, ROW_PSF, true>;
   s.row_std_batch[ROW_FFT_W_NORMAL] = (const void*)row_pass_batch<N1, N2, ROW_FFT_W_NORMAL, true>;
   s.col_std_batch[COL_IFFT_PROD_FFT] = (const void*)col_pass_batch<N1, N2, COL_IFFT_PROD_FFT, true>;

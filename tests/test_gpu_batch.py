@@ -125,3 +125,24 @@ def test_batch_profile_times_every_cg_kernel(data):
                       [_t(torch, frames[i][1].mask, dev) for i in (0, 1)])
         ms = b.profile_cg(reps=2)
     assert len(ms) == 6 and all(v > 0 for v in ms.values())
+
+
+def test_multi_side_launches_match_per_side_launches(data, monkeypatch):
+    # NLINV_BATCH_MULTI=1: one launch per pass for the frames of every grid side in 128..384 together (the block
+    # dispatches on its frame's side), instead of one launch per pass and side.  Same pass bodies, same block
+    # partition of each frame, so the two forms agree to the FP32 operator tolerance.
+    torch, _ = data
+    from paper_1301_1215_gb300.nlinv import NlinvBatch
+    shapes = [(128, 4, 12), (192, 5, 15), (128, 6, 9), (256, 3, 11)]
+    frames = [noisy_data(n, J, S, 3100 + i) for i, (n, J, S) in enumerate(shapes)]
+    dev = torch.device("cuda")
+    ys = [_t(torch, y, dev) for _, _, y in frames]
+    ms = [_t(torch, fr.mask, dev) for _, fr, _ in frames]
+    out = {}
+    for multi in ("0", "1"):
+        monkeypatch.setenv("NLINV_BATCH_MULTI", multi)
+        with NlinvBatch([(n, J) for n, J, _ in shapes], newton_steps=3, cg_iters=8) as b:
+            out[multi] = [x.cpu().numpy() for x in b.reconstruct(ys, ms)]
+    for i, (a, c) in enumerate(zip(out["0"], out["1"])):
+        assert np.isfinite(c).all(), i
+        assert rel(c, a) < 1e-5, i
