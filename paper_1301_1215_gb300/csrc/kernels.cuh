@@ -317,26 +317,28 @@ constexpr int kRowCtasPerSM = 2;
 // before adding them to its FP64 partial, so the FP32 summation length is bounded whatever the problem size.
 template <int N, int MODE, bool STDF>
 __device__ __forceinline__ double rho_slice(const KArgs& A, int bid) {
+  // pixel and channel-product offsets in 32 bits: a plane has at most 1024^2 pixels, the J channel-product planes
+  // at most 64 x 512^2 entries
   const int f = STDF ? N / 4 : A.f, Wc = STDF ? N / 2 : A.Wc, J = A.J;
-  constexpr long plane = (long)N * N;
-  const long e_begin = (long)bid * A.rho_per_cta;
-  const long e_end = e_begin + A.rho_per_cta < plane ? e_begin + A.rho_per_cta : plane;
+  constexpr int plane = N * N;
+  const int e_begin = bid * A.rho_per_cta;
+  const int e_end = min(e_begin + A.rho_per_cta, plane);
   const float beta = (MODE == ROW_FFT_W_NORMAL && A.pupd) ? cg_beta(A) : 0.f;
-  const size_t stride = (size_t)Wc * Wc;
-  const long bd = blockDim.x;
+  const int stride = Wc * Wc;
+  const int bd = blockDim.x;
   double accd = 0.0;
-  for (long o0 = e_begin + threadIdx.x; o0 < e_end; o0 += 2 * bd) {
+  for (int o0 = e_begin + threadIdx.x; o0 < e_end; o0 += 2 * bd) {
     float acc = 0.f;
     float2 a[2], b[2];
-    const float2* zp[2];
+    int zo[2];
     bool ok[2], om[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const long o = o0 + k * bd;
-      const int e1 = (int)(o / N), e2 = (int)(o % N);
+      const int o = o0 + k * bd;
+      const int e1 = o / N, e2 = o - e1 * N;
       ok[k] = o < e_end;
       om[k] = ok[k] && in_omega(e1, N, f) && in_omega(e2, N, f);
-      zp[k] = A.zsum + (om[k] ? (size_t)to_compact(e1, N, f) * Wc + to_compact(e2, N, f) : 0);
+      zo[k] = om[k] ? to_compact(e1, N, f) * Wc + to_compact(e2, N, f) : 0;
       a[k] = b[k] = make_float2(0.f, 0.f);
       if (ok[k]) {
         if constexpr (MODE == ROW_FFT_W_NORMAL) {
@@ -352,18 +354,20 @@ __device__ __forceinline__ double rho_slice(const KArgs& A, int bid) {
     float2 z00 = zero, z01 = zero, z10 = zero, z11 = zero;
     int j = 0;
     for (; j + 2 <= J; j += 2) {
-      if (om[0]) { z00 = cadd(z00, zp[0][j * stride]); z01 = cadd(z01, zp[0][(j + 1) * stride]); }
-      if (om[1]) { z10 = cadd(z10, zp[1][j * stride]); z11 = cadd(z11, zp[1][(j + 1) * stride]); }
+      if (om[0]) { z00 = cadd(z00, A.zsum[zo[0]]); z01 = cadd(z01, A.zsum[zo[0] + stride]); }
+      if (om[1]) { z10 = cadd(z10, A.zsum[zo[1]]); z11 = cadd(z11, A.zsum[zo[1] + stride]); }
+      zo[0] += 2 * stride;
+      zo[1] += 2 * stride;
     }
     if (j < J) {
-      if (om[0]) z00 = cadd(z00, zp[0][j * stride]);
-      if (om[1]) z10 = cadd(z10, zp[1][j * stride]);
+      if (om[0]) z00 = cadd(z00, A.zsum[zo[0]]);
+      if (om[1]) z10 = cadd(z10, A.zsum[zo[1]]);
     }
     const float2 z[2] = {cadd(z00, z01), cadd(z10, z11)};
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       if (!ok[k]) continue;
-      const long o = o0 + k * bd;
+      const int o = o0 + k * bd;
       if constexpr (MODE == ROW_FFT_W_ADJ) {
         A.dst[o] = z[k];
       } else if constexpr (MODE == ROW_FFT_W_NORMAL) {
