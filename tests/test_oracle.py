@@ -177,6 +177,29 @@ def test_forward_reproduces_signal_equation_data():
     assert rel(O.forward(s, fr.mask, x), O.simulate(s, fr.mask, fr.rho, fr.coils)) < 1e-12
 
 
+def test_simulate_ignores_the_image_outside_omega():
+    # Eq. 2 restricts the image to Omega (M_Omega) before the coil product, so the data of a rho that also has
+    # content outside Omega equal those of its restriction to Omega, and differ from the unrestricted product's.
+    n, J, fov = 32, 3, 8
+    s = O.Setup(n, J, fov)
+    rng = synth.rng_for(23)
+    rho = synth.random_complex((n, n), rng)
+    c = synth.random_complex((J, n, n), rng)
+    mask = synth.radial_mask(n, 9)
+    inside = O.omega_mask(n, fov)
+    assert inside.sum() < n * n
+    y = O.simulate(s, mask, rho, c)
+    assert rel(y, O.simulate(s, mask, inside * rho, c)) < 1e-14
+    assert rel(y, mask * np.fft.fft2(rho * c, norm="ortho")) > 0.1
+
+
+def test_inner_product_conjugates_its_first_argument():
+    # Table 1's scalar product <u, v> = sum conj(u) v, on values worked by hand
+    assert O.inner(np.array([1j]), np.array([1.0])) == -1j
+    assert O.inner(np.array([1.0, 2j]), np.array([3.0, 1.0])) == 3 - 2j
+    assert O.inner(np.array([[2 - 1j]]), np.array([[1j]])) == (2 + 1j) * 1j
+
+
 def setup_random(n=32, J=3, fov=8, seed=13):
     s = O.Setup(n, J, fov)
     rng = synth.rng_for(seed)

@@ -143,3 +143,19 @@ def test_cg_stops_on_non_positive_curvature():
     info = {}
     dx = O.cg(lambda v: A @ v, np.array([1.0, 1.0], complex), 5, info)
     assert info["stop"] == 0 and not dx.any()
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_cg_floor_is_relative_to_the_right_hand_side(scale):
+    # CG is scale-equivariant: b -> s b gives dx -> s dx in exact arithmetic, and a floor relative to |b| stops
+    # on the same iteration (the scaled arithmetic rounds differently, hence the 1e-12 comparison)
+    rng = synth.rng_for(29)
+    B = synth.random_complex((12, 8), rng)
+    A = B.conj().T @ B + 0.1 * np.eye(8)
+    b = synth.random_complex((8,), rng)
+    ref_info, info = {}, {}
+    ref = O.cg(lambda v: A @ v, b, 8, ref_info)
+    got = O.cg(lambda v: A @ v, scale * b, 8, info)
+    assert info["stop"] == ref_info["stop"]
+    assert np.linalg.norm(got / scale - ref) < 1e-12 * np.linalg.norm(ref)
+
