@@ -379,6 +379,9 @@ def run_ours(args, rank, world, local):
         line["roofline"]["compulsory"]["note"] = line["roofline"]["compulsory"]["note"].replace(
             "all CG iterations' bytes", "the executed CG iterations' bytes")
     ctx.close()
+    if world > 1:       # replicas: the series alone; the single-GPU legs below would only hold every GPU longer
+        line["extras"] = "batch64, precision_512 and cpu_baseline are measured at N = 1 only"
+        return line
     if not args.no_batch:
         line["batch64"] = batch_compare(torch, dev, K=3, Wm=1)
     if not args.no_precision:
