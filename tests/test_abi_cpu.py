@@ -174,3 +174,21 @@ def test_every_kernel_waits_for_its_predecessor():
     assert "pdl_enter();" in enter[:200]
     # the deferred wait of the early-load path comes before the first store of a round
     assert body.index("if (!waited)") < body.index("A.dst[")
+
+
+def test_every_specialised_pass_has_batched_and_multi_side_forms():
+    # A single-frame pass specialised for the standard field of view (SizeKernels::row_std / col_std) is mapped to
+    # its batched form (row_std_batch / col_std_batch) and, with NLINV_BATCH_MULTI=1, to the multi-side kernel
+    # (MultiKernels::row_std / col_std); a mode missing from either table would leave batches without a kernel.
+    csrc = os.path.join(ROOT, "paper_1301_1215_gb300", "csrc")
+    kern = open(os.path.join(csrc, "kernels.cuh")).read()
+    body = kern[kern.index("template <int N1, int N2> SizeKernels make_size_kernels() {"):]
+    body = body[:body.index("\n}\n")]
+    multi = open(os.path.join(csrc, "batch_multi.cu")).read()
+    for side in ("row", "col"):
+        single = set(re.findall(rf"s\.{side}_std\[(\w+)\] =", body))
+        batched = set(re.findall(rf"s\.{side}_std_batch\[(\w+)\] =", body))
+        multi_std = set(re.findall(rf"m\.{side}_std\[(\w+)\] =", multi))
+        assert single, side
+        assert single == batched, (side, single ^ batched)
+        assert single == multi_std, (side, single ^ multi_std)
