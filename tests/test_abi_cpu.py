@@ -55,9 +55,13 @@ def test_default_params(lib):
     assert lib.nlinv_default_params(None, 64, 4) == _lib.EINVAL
 
 
-@pytest.mark.parametrize("field,value", [("n", 100), ("ncoils", 0), ("newton_steps", 0), ("newton_steps", 65),
-                                         ("cg_iters", -1), ("alpha0", 0.0), ("alpha_q", 1.5), ("alpha_min", -1.0),
-                                         ("sobolev_a", -1.0), ("fov", 0), ("fov", 33)])
+@pytest.mark.parametrize("field,value", [("n", 100), ("ncoils", 0), ("ncoils", 65), ("newton_steps", 0),
+                                         ("newton_steps", 65), ("cg_iters", -1), ("cg_iters", 100001),
+                                         ("alpha0", 0.0), ("alpha0", float("nan")), ("alpha0", float("inf")),
+                                         ("alpha_q", 0.0), ("alpha_q", 1.5), ("alpha_min", -1.0),
+                                         ("alpha_min", float("nan")), ("sobolev_a", -1.0), ("sobolev_a", float("nan")),
+                                         ("sobolev_l", -1.0), ("sobolev_l", float("inf")), ("fov", 0), ("fov", 33),
+                                         ("tensor_dft", 2), ("tensor_dft", 1)])
 def test_create_rejects_bad_params_before_touching_cuda(lib, field, value):
     from paper_1301_1215_gb300 import _lib
     p = _lib.Params()
