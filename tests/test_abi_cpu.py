@@ -196,3 +196,25 @@ def test_every_specialised_pass_has_batched_and_multi_side_forms():
         assert single, side
         assert single == batched, (side, single ^ batched)
         assert single == multi_std, (side, single ^ multi_std)
+
+
+def test_forward_noalloc_checks_its_arguments_on_the_host(lib):
+    # every rejection below happens before the entry point asks CUDA for anything (the pointers are never read)
+    from paper_1301_1215_gb300 import _lib
+    E = _lib.EINVAL
+    dummy = C.c_void_p(16)
+    p = _lib.Params()
+    lib.nlinv_default_params(C.byref(p), 64, 4)
+    assert lib.nlinv_forward_noalloc(None, None, dummy, dummy, dummy) == E
+    assert lib.nlinv_forward_noalloc(C.byref(p), None, None, dummy, dummy) == E
+    assert lib.nlinv_forward_noalloc(C.byref(p), None, dummy, None, dummy) == E
+    assert lib.nlinv_forward_noalloc(C.byref(p), None, dummy, dummy, None) == E
+    for field, value in (("n", 100), ("ncoils", 0), ("fov", 0), ("fov", 33), ("sobolev_a", float("nan"))):
+        q = _lib.Params()
+        lib.nlinv_default_params(C.byref(q), 64, 4)
+        setattr(q, field, value)
+        assert lib.nlinv_forward_noalloc(C.byref(q), None, dummy, dummy, dummy) == E, field
+    big = _lib.Params()
+    lib.nlinv_default_params(C.byref(big), 512, 16)          # needs more than the static scratch array
+    assert lib.nlinv_forward_noalloc(C.byref(big), None, dummy, dummy, dummy) == E
+    assert b"static maximum" in lib.nlinv_last_error(None)
